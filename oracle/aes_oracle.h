@@ -1,0 +1,66 @@
+/*
+ * aes_oracle.h -- interface of the CPU oracle (test infrastructure only; see aes_oracle.c).
+ * This header belongs to the oracle alone: the product library neither includes it nor
+ * links the oracle, and the oracle includes nothing of the product.
+ *
+ * Conventions: a block is 16 bytes in the paper's column-major state order (byte i is row
+ * i % 4, column i / 4).  A key schedule is (Nr + 1) round keys of 16 bytes, laid out
+ * contiguously.  `iv` may be NULL (no IV added: plain ECB).
+ */
+#ifndef AES_ORACLE_H
+#define AES_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* GF(2^8) with modulus x^8 + x^4 + x^3 + x + 1 (Section II) */
+uint8_t oracle_gf_add(uint8_t a, uint8_t b);
+uint8_t oracle_gf_mul(uint8_t a, uint8_t b);
+uint8_t oracle_gf_inv(uint8_t a); /* exhaustive search, inv(0) = 0 (App. A2) */
+
+/* affine maps of App. A2 (S-box) and App. A5 (inverse S-box) */
+uint8_t oracle_affine(uint8_t x);
+uint8_t oracle_inv_affine(uint8_t x);
+uint8_t oracle_sbox(uint8_t x);     /* affine(inv(x)), App. A2 */
+uint8_t oracle_inv_sbox(uint8_t x); /* inv(inv_affine(x)), App. A5 */
+
+/* round steps on one 16-byte state, in place */
+void oracle_sub_bytes(uint8_t s[16]);
+void oracle_inv_sub_bytes(uint8_t s[16]);
+void oracle_shift_rows(uint8_t s[16]);
+void oracle_inv_shift_rows(uint8_t s[16]);
+void oracle_mix_columns(uint8_t s[16]);
+void oracle_inv_mix_columns(uint8_t s[16]);
+void oracle_add(uint8_t s[16], const uint8_t k[16]);
+
+/* key schedule: returns Nr (10, 12, 14) and writes 16*(Nr+1) bytes, or -1 on a bad size */
+uint8_t oracle_rcon(int r); /* x^(r-1), App. A3 */
+int oracle_key_expand(const uint8_t* key, int key_bits, uint8_t* rk_out);
+int oracle_key_expand_words(const uint8_t* key, int nk, uint8_t* rk_out);
+
+/* one block: C = Cipher(P + iv), P = InvCipher(C) + iv (App. A1 / A4 with one block) */
+void oracle_encrypt_block(const uint8_t* rk, int nr, const uint8_t iv[16], const uint8_t in[16],
+                          uint8_t out[16]);
+void oracle_decrypt_block(const uint8_t* rk, int nr, const uint8_t iv[16], const uint8_t in[16],
+                          uint8_t out[16]);
+
+/* many independent blocks over `nthreads` host threads; in == out allowed; returns 0 */
+int oracle_encrypt_blocks(const uint8_t* rk, int nr, const uint8_t* iv, const uint8_t* in,
+                          uint8_t* out, size_t nblocks, int nthreads);
+int oracle_decrypt_blocks(const uint8_t* rk, int nr, const uint8_t* iv, const uint8_t* in,
+                          uint8_t* out, size_t nblocks, int nthreads);
+
+/* CBC chaining over the nblocks blocks of ONE message (Section II, App. A1, A4) */
+void oracle_cbc_encrypt(const uint8_t* rk, int nr, const uint8_t iv[16], const uint8_t* in,
+                        uint8_t* out, size_t nblocks);
+void oracle_cbc_decrypt(const uint8_t* rk, int nr, const uint8_t iv[16], const uint8_t* in,
+                        uint8_t* out, size_t nblocks);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
