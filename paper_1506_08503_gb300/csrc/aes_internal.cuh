@@ -1,0 +1,71 @@
+// aes_internal.cuh -- declarations shared by the library's translation units (not part of
+// the C ABI; include/aesgb.h is the public surface).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "aes_field.cuh"
+#include "aesgb.h"
+
+namespace aesgb {
+
+constexpr int kMaxRounds = 14;
+
+// Round keys as little-endian column words, passed by value as a kernel parameter so that
+// every AddRoundKey reads its operand from the constant bank (no memory traffic per block).
+struct KeyWords {
+  uint32_t w[kMaxRounds + 1][4];
+};
+
+
+// ---- errors -------------------------------------------------------------------------
+aes_status set_error(aes_status st, const char* fmt, ...);
+aes_status cuda_error(cudaError_t e, const char* what);
+void clear_error();
+
+// ---- device facts ---------------------------------------------------------------------
+struct DeviceInfo {
+  int device = -1;
+  int sms = 0;
+  int smem_optin = 0;  // max dynamic shared memory per block (bytes)
+  char name[256] = {0};
+};
+// Info for the current device (cached per device).  Returns nullptr and sets the error on
+// a CUDA failure.
+const DeviceInfo* current_device_info();
+
+// ---- key words -------------------------------------------------------------------------
+// Encryption: round key 0 has the IV folded in (C = E(P ^ IV) needs P ^ IV ^ K0).
+KeyWords enc_key_words(const aes_key_schedule& ks, const uint8_t* iv);
+// Decryption, equivalent inverse cipher: word r is InvMixColumns(K[nr - r]) for
+// 0 < r < nr, K[nr] first, K[0] ^ IV last (P = D(C) ^ IV).
+KeyWords dec_key_words(const aes_key_schedule& ks, const uint8_t* iv);
+bool schedule_ok(const aes_key_schedule* ks);
+
+// ---- launch configurations --------------------------------------------------------------
+struct TTConfig {
+  int threads = 512;  // CTA size (see tt::select_config for the compiled pairs)
+  int unroll = 2;     // blocks per thread in flight
+  int ctas_per_sm = 1;
+};
+
+struct BSConfig {
+  int threads = 128;  // CTA size: 64, 128 or 256 (each thread owns 32 blocks)
+};
+
+using TTKernelFn = void (*)(const uint4*, uint4*, size_t, const KeyWords);
+TTKernelFn ttable_kernel_r10(int dir, int threads, int unroll);
+TTKernelFn ttable_kernel_r12(int dir, int threads, int unroll);
+TTKernelFn ttable_kernel_r14(int dir, int threads, int unroll);
+
+aes_status launch_ttable(int dir, int nr, const KeyWords& kw, const void* d_in, void* d_out,
+                         size_t nblocks, cudaStream_t stream, const TTConfig& cfg);
+aes_status launch_bitslice(int dir, int nr, const KeyWords& kw, const void* d_in, void* d_out,
+                           size_t nblocks, cudaStream_t stream, const BSConfig& cfg);
+
+// Shared-memory bytes one T-table CTA needs for direction `dir`.
+size_t ttable_smem_bytes(int dir);
+
+}  // namespace aesgb

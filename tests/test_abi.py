@@ -1,0 +1,89 @@
+"""The C ABI on the host, no GPU needed: the library loads, exports every function that
+include/*.h declares, expands keys exactly like the oracle, and rejects bad arguments before
+any CUDA call."""
+import ctypes
+import re
+import subprocess
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions() -> set[str]:
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(aes_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_core_entry_points():
+    names = declared_functions()
+    for n in ("aes_key_expand", "aes_encrypt_blocks", "aes_decrypt_blocks", "aes_crypt_blocks", "aes_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(aes):
+    lib = aes.lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", str(aes.LIB_PATH)], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = sorted(n for n in declared_functions() if n not in exported)
+    assert not missing, missing
+    for n in declared_functions():
+        assert getattr(lib, n) is not None
+    # the Python binding mirrors the same names
+    assert set(aes.declared_symbols()) <= declared_functions()
+
+
+@pytest.mark.parametrize("bits", [128, 192, 256])
+def test_key_expand_matches_oracle(aes, orc, bits):
+    rng = np.random.default_rng(bits)
+    for _ in range(200):
+        key = rng.integers(0, 256, bits // 8, dtype=np.uint8)
+        ks = aes.aes_key_expand(key.tobytes(), bits)
+        rk, nr = orc.key_expand(key, bits)
+        assert ks.nr == nr
+        assert ks.round_keys() == rk.tobytes()
+        tail = bytes(bytearray(ks.rk))[16 * (nr + 1):]
+        assert tail == bytes(len(tail))
+
+
+def test_key_expand_rejects_bad_sizes(aes):
+    ks = aes.aes_key_schedule()
+    key = (ctypes.c_uint8 * 32)()
+    for bits in (0, 64, 160, 512, -128):
+        assert aes.lib().aes_key_expand(key, bits, ctypes.byref(ks)) == aes.AES_EINVAL
+        assert "key_bits" in aes.aes_last_error()
+    assert aes.lib().aes_key_expand(None, 128, ctypes.byref(ks)) == aes.AES_EINVAL
+    assert aes.lib().aes_key_expand(key, 128, None) == aes.AES_EINVAL
+
+
+def test_crypt_argument_checks_before_any_cuda_call(aes):
+    lib = aes.lib()
+    ks = aes.aes_key_expand(bytes(16))
+    kp = ctypes.byref(ks)
+    base = 1 << 40  # never dereferenced: every call below fails validation first
+    assert lib.aes_crypt_blocks(kp, None, base, base + 4096, 0, 0, 0, None) == aes.AES_OK  # empty
+    assert lib.aes_crypt_blocks(kp, None, base + 8, base + 4096, 4, 0, 0, None) == aes.AES_EINVAL  # misaligned
+    assert lib.aes_crypt_blocks(kp, None, base, base + 16, 4, 0, 0, None) == aes.AES_EINVAL  # partial overlap
+    assert lib.aes_crypt_blocks(kp, None, None, base, 4, 0, 0, None) == aes.AES_EINVAL
+    assert lib.aes_crypt_blocks(kp, None, base, base + 4096, 4, 2, 0, None) == aes.AES_EINVAL  # bad dir
+    assert lib.aes_crypt_blocks(kp, None, base, base + 4096, 4, 0, 9, None) == aes.AES_EINVAL  # bad impl
+    assert lib.aes_crypt_blocks(kp, None, base, base + 4096, 1 << 62, 0, 0, None) == aes.AES_EINVAL  # too big
+    bad = aes.aes_key_schedule()
+    bad.nr = 11
+    assert lib.aes_crypt_blocks(ctypes.byref(bad), None, base, base + 4096, 4, 0, 0, None) == aes.AES_EINVAL
+    assert lib.aes_crypt_blocks(None, None, base, base + 4096, 4, 0, 0, None) == aes.AES_EINVAL
+    assert aes.aes_last_error()
+
+
+def test_binding_raises_with_message(aes):
+    ks = aes.aes_key_expand(bytes(16))
+    with pytest.raises(aes.AesError) as ei:
+        aes.aes_crypt_blocks(ks, None, (1 << 40) + 8, 1 << 41, 4, "encrypt")
+    assert ei.value.status == aes.AES_EINVAL and "aligned" in str(ei.value)
