@@ -103,6 +103,81 @@ aes_status aes_crypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, const
 aes_status aes_crypt_host(const aes_key_schedule* ks, const uint8_t* iv, const void* h_in, void* h_out,
                           size_t nblocks, int dir, int impl, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Key pool: expanded schedules resident in device memory, addressed by index.  The paper's
+ * key tensor K (R x N x 16, Section II) with one schedule per message.
+ * ------------------------------------------------------------------------------------- */
+typedef struct aes_keypool aes_keypool;
+
+/* Allocates device memory for `capacity` schedules (512 bytes each) on the current device.
+ * capacity must be 1..2^24, else AES_EINVAL; AES_ENOMEM if the allocation fails.  The pool
+ * is owned by the library until aes_keypool_destroy. */
+aes_status aes_keypool_create(size_t capacity, aes_keypool** out);
+
+/* Expands `count` raw keys (host pointer, count * key_bits/8 bytes, back to back) ON THE
+ * DEVICE into slots first .. first+count-1, together with their equivalent-inverse-cipher
+ * schedules for decryption.  key_bits: 128, 192 or 256.  Returns once the schedules are
+ * resident (it synchronises `cuda_stream`).  Slots out of range are AES_EINVAL. */
+aes_status aes_keypool_load_keys(aes_keypool* pool, uint32_t first, size_t count, const uint8_t* keys,
+                                 int key_bits, void* cuda_stream);
+
+/* Copies one host-expanded schedule into slot `idx` (synchronous). */
+aes_status aes_keypool_set(aes_keypool* pool, uint32_t idx, const aes_key_schedule* ks);
+
+/* Number of rounds of slot idx (10, 12 or 14), or 0 if the slot was never loaded. */
+int aes_keypool_rounds(const aes_keypool* pool, uint32_t idx);
+
+/* Frees the pool's device memory.  NULL is a no-op.  The caller must not destroy a pool
+ * while work that uses it is still queued. */
+aes_status aes_keypool_destroy(aes_keypool* pool);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched messages: many messages, each with its own key slot, direction and length, in one
+ * persistent launch per direction (replayed from a CUDA graph).  Blocks of a message are
+ * independent (the paper's one-block CBC messages, i.e. ECB under that message's key).
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  uint32_t key_idx; /* slot in the key pool (must be loaded) */
+  uint32_t dir;     /* AES_ENCRYPT or AES_DECRYPT */
+  uint64_t offset;  /* byte offset into both buffers, a multiple of 16 */
+  uint64_t length;  /* bytes, a multiple of 16 (0 allowed: nothing to do) */
+} aes_msg;
+
+typedef struct aes_batch aes_batch;
+
+/* A reusable batch context bound to `pool`: device descriptor buffers, pinned staging and the
+ * cached CUDA graph.  max_msgs is the largest message count a single run may carry
+ * (1..2^24).  AES_ENOMEM if its buffers cannot be allocated. */
+aes_status aes_batch_create(aes_keypool* pool, size_t max_msgs, aes_batch** out);
+
+/* Runs every message of `msgs` (host array of nmsgs <= max_msgs) reading d_in and writing
+ * d_out (device pointers, each buf_bytes long, 16-byte aligned; d_in == d_out allowed).
+ * Asynchronous on cuda_stream; the host array may be reused as soon as the call returns.
+ * A message whose [offset, offset+length) leaves the buffers, a length or offset that is not
+ * a multiple of 16, an unloaded key slot or a bad dir is AES_EINVAL (nothing launched). */
+aes_status aes_batch_run(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const void* d_in, void* d_out,
+                         size_t buf_bytes, void* cuda_stream);
+
+/* Tunes the batch's launch shape (CTA size, blocks per thread per tile) on this workload:
+ * times every compiled candidate on `msgs` (it overwrites d_out), keeps the fastest and, if
+ * cache_path is not NULL, records it in that JSON file keyed by device name and workload
+ * signature (an existing entry is reused without timing).  Writes the chosen shape to
+ * *threads and *blocks_per_lane when they are not NULL. */
+aes_status aes_batch_autotune(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const void* d_in, void* d_out,
+                              size_t buf_bytes, const char* cache_path, int* threads, int* blocks_per_lane,
+                              void* cuda_stream);
+
+/* Sets the launch shape directly (see aes_batch_autotune for the meaning); AES_EINVAL for a
+ * shape that is not compiled. */
+aes_status aes_batch_set_shape(aes_batch* b, int threads, int blocks_per_lane);
+
+aes_status aes_batch_destroy(aes_batch* b);
+
+/* One-shot form of aes_batch_run through a batch context the pool keeps internally (created
+ * on first use and grown as needed).  Calls on one pool are serialised. */
+aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsgs, const void* d_in,
+                             void* d_out, size_t buf_bytes, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,7 +87,7 @@ extern "C" aes_status aes_crypt_host(const aes_key_schedule* ks, const uint8_t* 
     // stream order makes the slot's previous D2H finish before this H2D overwrites it
     if ((e = cudaMemcpyAsync(s->buf[slot], src + done * 16, n * 16, cudaMemcpyHostToDevice, str)) != cudaSuccess)
       return cuda_error(e, "cudaMemcpyAsync H2D");
-    if (impl == AES_IMPL_BITSLICE) st = launch_bitslice(dir, ks->nr, kw, s->buf[slot], s->buf[slot], n, str, BSConfig{});
+    if (impl == AES_IMPL_BITSLICE) st = launch_bitslice(dir, *ks, iv, s->buf[slot], s->buf[slot], n, str, BSConfig{});
     else st = launch_ttable(dir, ks->nr, kw, s->buf[slot], s->buf[slot], n, str, TTConfig{});
     if (st != AES_OK) return st;
     if ((e = cudaMemcpyAsync(dst + done * 16, s->buf[slot], n * 16, cudaMemcpyDeviceToHost, str)) != cudaSuccess)

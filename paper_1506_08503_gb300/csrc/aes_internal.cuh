@@ -52,7 +52,7 @@ struct TTConfig {
 };
 
 struct BSConfig {
-  int threads = 128;  // CTA size: 64, 128 or 256 (each thread owns 32 blocks)
+  int reserved = 0;  // one compiled shape: 128-thread CTAs, 32 blocks per thread
 };
 
 using TTKernelFn = void (*)(const uint4*, uint4*, size_t, const KeyWords);
@@ -62,8 +62,10 @@ TTKernelFn ttable_kernel_r14(int dir, int threads, int unroll);
 
 aes_status launch_ttable(int dir, int nr, const KeyWords& kw, const void* d_in, void* d_out,
                          size_t nblocks, cudaStream_t stream, const TTConfig& cfg);
-aes_status launch_bitslice(int dir, int nr, const KeyWords& kw, const void* d_in, void* d_out,
-                           size_t nblocks, cudaStream_t stream, const BSConfig& cfg);
+// The bitsliced kernels take the plain schedule (they run the paper's inverse-cipher order,
+// not the equivalent inverse cipher); the IV is folded into round key 0.
+aes_status launch_bitslice(int dir, const aes_key_schedule& ks, const uint8_t* iv, const void* d_in,
+                           void* d_out, size_t nblocks, cudaStream_t stream, const BSConfig& cfg);
 
 // Shared-memory bytes one T-table CTA needs for direction `dir`.
 size_t ttable_smem_bytes(int dir);
