@@ -35,7 +35,7 @@ import numpy as np
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-from paper_1506_08503_gb300 import workloads  # noqa: E402
+from paper_1506_08503_gb300 import sharding, workloads  # noqa: E402
 
 METRIC = "AES-128 encrypt+decrypt throughput, many independent 16-byte blocks"
 UNIT = "GB/s"
@@ -43,7 +43,7 @@ WORKLOAD = "aes128-enc+dec-1GiB-2^26-blocks-seed1"
 NBLOCKS = 1 << 26
 SEED = 1
 
-# On-chip integer roofline ("Roofline"): per SM and clock the GB300 issues
+# On-chip integer roofline: per SM and clock the GB300 issues
 # 64 lanes of integer ALU work (LOP3/PRMT/SHF/IADD, measured) and 32 lanes of shared-memory
 # loads.  A table-lookup AES-128 block needs at least 160 lookups and 240 ALU operations; a
 # gate-level (bitsliced) block at least 356.25 ALU lane-operations (22,800 two-input gates,
@@ -77,6 +77,9 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     p.add_argument("--nblocks", type=int, default=NBLOCKS, help="blocks per rank (default 2^26 = 1 GiB)")
+    p.add_argument("--no-batched", action="store_true", help="skip the 4096-message batched measurement")
+    p.add_argument("--no-served", action="store_true", help="skip the served (request server) measurement")
+    p.add_argument("--served-requests", type=int, default=10000, help="requests per offered rate")
     return p.parse_args()
 
 
@@ -204,6 +207,102 @@ def read_profile_traffic() -> float | None:
     return None
 
 
+def measure_batched(aes, torch, dev, steps: int, plain_gbs: float) -> dict:
+    """4096 messages, lognormal lengths (median 4 KiB, sigma 1.5), one AES-128 key each (seed 3),
+    encrypted in one autotuned persistent launch per step; L2 is flushed between steps."""
+    m = workloads.batched_messages(3)
+    total = int(m.lengths.sum())
+    msgs = np.zeros(len(m.lengths), dtype=aes.msg_dtype())
+    msgs["key_idx"] = np.arange(len(m.lengths))
+    msgs["offset"], msgs["length"] = m.offsets, m.lengths
+    stream = torch.cuda.current_stream()
+    with aes.KeyPool(len(m.keys)) as pool:
+        pool.load_keys(0, m.keys, 128)
+        x = torch.from_numpy(m.data).to(dev)
+        y = torch.empty_like(x)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        with aes.Batch(pool, len(m.lengths)) as b:
+            shape = b.autotune(msgs, x.data_ptr(), y.data_ptr(), total)
+            for _ in range(3):
+                b.run(msgs, x.data_ptr(), y.data_ptr(), total)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k in range(steps):
+                flush.fill_(k & 0xFF)
+                evs[k][0].record(stream)
+                b.run(msgs, x.data_ptr(), y.data_ptr(), total)
+                evs[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = [a.elapsed_time(c) for a, c in evs]
+    gbs = total * len(ms) / (sum(ms) / 1e3) / 1e9
+    return {"workload": "4096 msgs, lognormal(median 4 KiB, sigma 1.5) in [16 B, 16 MiB], own AES-128 key each, seed 3",
+            "bytes": total, "value": gbs, "unit": UNIT, "ms_per_batch": sum(ms) / len(ms),
+            "shape": {"threads": shape[0], "blocks_per_lane": shape[1]},
+            "vs_plain_kernel": gbs / plain_gbs if plain_gbs else None,
+            "l2": "flushed (256 MiB write) before every timed batch", "launch": "aes_batch_run (CUDA graph replay)"}
+
+
+def measure_served(aes, torch, dev, nreq: int, plain_gbs: float) -> dict:
+    """The request server under Poisson arrivals (seed 4): 50/50 encrypt/decrypt, sizes
+    lognormal (median 4 KiB, sigma 1.5) in [64 B, 64 MiB], keys from a resident pool of 1024
+    (512 AES-128, 512 AES-256), payloads resident in device memory.  Offered rates 1k, 10k
+    and 100k requests/s, then a closed loop (everything submitted at once) for saturation."""
+    import time as _t
+
+    out = {"workload": "Poisson arrivals, 50/50 enc/dec, lognormal(median 4 KiB, sigma 1.5) in [64 B, 64 MiB], "
+                       "1024-key pool (half AES-128, half AES-256), device-resident payloads, seed 4",
+           "requests_per_rate": nreq, "rates": []}
+    w0 = workloads.served_requests(4, 1, 1.0)
+    pool = aes.KeyPool(len(w0.pool_keys))
+    pool.load_keys(0, np.stack(w0.pool_keys[:512]), 128)
+    pool.load_keys(512, np.stack(w0.pool_keys[512:]), 256)
+    srv = aes.Server(pool, hbm_budget=1 << 30, max_inflight=1 << 20, nstreams=4, max_batch=8192,
+                     queue_capacity=1 << 22)
+    try:
+        for rate in (1000.0, 10000.0, 100000.0, None):
+            w = workloads.served_requests(4, nreq if rate else 4 * nreq, rate or 1e9)
+            offs = np.concatenate([[0], np.cumsum(w.lengths)[:-1]]).astype(np.int64)
+            total = int(w.lengths.sum())
+            src = torch.randint(0, 256, (total,), dtype=torch.uint8, device=dev)
+            dst = torch.empty_like(src)
+            torch.cuda.synchronize()
+            sp, dp = src.data_ptr(), dst.data_ptr()
+            srv.reset_stats()
+            tickets = []
+            t0 = _t.perf_counter()
+            if rate:
+                for i in range(len(w.lengths)):
+                    target = t0 + w.arrival_s[i]
+                    while _t.perf_counter() < target:
+                        pass
+                    o = int(offs[i])
+                    tickets.append(srv.submit(int(w.key_idx[i]), int(w.dirs[i]), sp + o, dp + o, int(w.lengths[i]),
+                                              True, True))
+            else:  # closed loop: the whole workload queued in bulk, the server batches what it finds
+                reqs = np.zeros(len(w.lengths), dtype=aes.request_dtype())
+                reqs["key_idx"], reqs["dir"], reqs["length"] = w.key_idx, w.dirs, w.lengths
+                reqs["src"], reqs["dst"] = sp + offs, dp + offs
+                reqs["src_on_device"], reqs["dst_on_device"] = 1, 1
+                for k in range(0, len(reqs), 4096):
+                    tickets.extend(srv.submit_many(reqs[k:k + 4096]).tolist())
+            states = [srv.poll(t) for t in tickets]
+            st = srv.stats()
+            entry = {"offered_rate": rate if rate else "closed-loop", "requests": len(tickets),
+                     "achieved_rate": len(tickets) / max(1e-9, _t.perf_counter() - t0),
+                     "p50_us": st["p50_us"], "p99_us": st["p99_us"], "max_us": st["max_us"], "gbps": st["gbps"],
+                     "mean_batch": st["mean_batch"], "launches": st["launches"],
+                     "failed": int(sum(1 for x in states if x != aes.AES_REQ_DONE)), "bytes": total}
+            if rate is None:
+                entry["vs_plain_kernel"] = st["gbps"] / plain_gbs if plain_gbs else None
+                out["closed_loop"] = entry
+            else:
+                out["rates"].append(entry)
+            del src, dst
+    finally:
+        srv.close()
+        pool.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -226,7 +325,7 @@ def run_ours(args):
 
     n = args.nblocks
     # weak scaling: every rank processes its own 1 GiB batch (rank 0 holds the seed-1 data)
-    w = workloads.plain(SEED + 1000 * rank, n)
+    w = workloads.plain(sharding.weak_scaling_seed(SEED, rank), n)
     x = torch.from_numpy(w.data).to(dev)
     ct = torch.empty_like(x)
     pt = torch.empty_like(x)
@@ -282,11 +381,7 @@ def run_ours(args):
     if not torch.equal(pt, x):
         raise RuntimeError("round trip failed after the timed region")
 
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = sharding.max_over_ranks(ms, dev)
     bytes_per_step_rank = 2 * n * 16
     value = bytes_per_step_rank * world * args.steps / (ms_max / 1e3) / 1e9
 
@@ -314,10 +409,7 @@ def run_ours(args):
             host_step()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
-        if dist is not None:
-            tt = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = sharding.max_over_ranks(dt, dev)
         if not torch.equal(hp, hx):
             raise RuntimeError("host-buffer round trip failed")
         e2e = {"value": bytes_per_step_rank * world * e2e_steps / dt / 1e9, "unit": UNIT,
@@ -338,6 +430,14 @@ def run_ours(args):
                 "peak_source": f"derived: {sms} SMs x {SM_MAX_MHZ_NOMINAL:.0f} MHz x {blocks_per_sm_clock():.4f} blocks/SM-clock x 16 B",
                 "enc_gbs": n * 16 / (enc_avg / 1e3) / 1e9, "dec_gbs": n * 16 / (dec_avg / 1e3) / 1e9,
                 "hbm_term_gbs": 6774.2 / 2}
+
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = measure_batched(aes, torch, dev, max(10, min(args.steps, 50)), roofline["enc_gbs"])
+
+    served = None
+    if not args.no_served and rank == 0:
+        served = measure_served(aes, torch, dev, args.served_requests, roofline["enc_gbs"])
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ---------------------------------------------
     cpu = None
@@ -365,7 +465,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "nblocks_per_rank": n, "key_bits": 128, "mode": "ECB (IV = 0)",
                        "kernel": args.kernel, "l2": "inputs (1 GiB) larger than L2 (129 MB); no flush"},
             "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk, "roofline": roofline,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "batched": batched, "served": served,
         }
         print(json.dumps(line))
     if dist is not None:

@@ -158,7 +158,9 @@ aes_status aes_batch_create(aes_keypool* pool, size_t max_msgs, aes_batch** out)
 aes_status aes_batch_run(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const void* d_in, void* d_out,
                          size_t buf_bytes, void* cuda_stream);
 
-/* Tunes the batch's launch shape (CTA size, blocks per thread per tile) on this workload:
+/* Tunes the batch's launch shape on this workload: the CTA size and the blocks each lane
+ * enciphers per window; compiled pairs are (512, 1), (512, 2), (512, 4), (384, 4), (256, 4),
+ * one CTA per SM.  It
  * times every compiled candidate on `msgs` (it overwrites d_out), keeps the fastest and, if
  * cache_path is not NULL, records it in that JSON file keyed by device name and workload
  * signature (an existing entry is reused without timing).  Writes the chosen shape to
@@ -177,6 +179,74 @@ aes_status aes_batch_destroy(aes_batch* b);
  * on first use and grown as needed).  Calls on one pool are serialised. */
 aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsgs, const void* d_in,
                              void* d_out, size_t buf_bytes, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Request server with continuous batching.  A host thread owned by the server admits queued
+ * requests while device staging memory (the HBM budget) and in-flight slots are free, packs
+ * them into one batched launch per CUDA stream, and starts the next batch on another stream
+ * as soon as one is free, so requests that arrive while others run join the next launch
+ * instead of waiting for a full drain.  Key schedules stay resident in the key pool.
+ * ------------------------------------------------------------------------------------- */
+typedef struct aes_server aes_server;
+
+typedef struct {
+  uint64_t hbm_budget;      /* device bytes for staging host payloads (>= 1 MiB) */
+  uint32_t max_inflight;    /* requests admitted but not completed (>= 1) */
+  uint32_t nstreams;        /* concurrent batches, 1..16 */
+  uint32_t max_batch;       /* requests per launch, 1..65536 */
+  uint32_t queue_capacity;  /* submitted but not admitted requests before AES_EAGAIN (>= 1) */
+  uint32_t fail_every;      /* fault injection for tests: every n-th launch fails on the host
+                               without touching the GPU (its requests end FAILED); 0 = off */
+  uint32_t reserved;
+} aes_server_cfg;
+
+typedef struct {
+  uint32_t key_idx;        /* loaded key-pool slot */
+  uint32_t dir;            /* AES_ENCRYPT or AES_DECRYPT */
+  const void* src;         /* input: device pointer if src_on_device, else host pointer */
+  void* dst;               /* output: device pointer if dst_on_device, else host pointer */
+  uint64_t length;         /* bytes, a multiple of 16, > 0 */
+  uint32_t src_on_device;  /* 1: src is device memory (16-byte aligned) */
+  uint32_t dst_on_device;  /* 1: dst is device memory (16-byte aligned) */
+} aes_request;
+
+#define AES_REQ_PENDING 0
+#define AES_REQ_DONE 1
+#define AES_REQ_FAILED 2
+
+typedef struct {
+  uint64_t submitted, completed, failed, queued, inflight, launches;
+  uint64_t bytes_completed;
+  double p50_us, p99_us, max_us, mean_us; /* submit-to-completion latency of completed requests */
+  double gbps;                            /* bytes_completed / (last completion - first submit) */
+  double mean_batch;                      /* requests per launch */
+} aes_server_stats;
+
+/* Starts a server on the current device over `pool` (which must outlive the server).  The
+ * staging arena of cfg->hbm_budget bytes is allocated now; AES_ENOMEM if it does not fit. */
+aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_server** out);
+
+/* Queues a copy of *req and returns its ticket.  The caller keeps src/dst alive and untouched
+ * until the ticket is reported done.  AES_EAGAIN if the queue is full, AES_EINVAL for a bad
+ * request, AES_ENOMEM if it needs more staging than the whole budget. */
+aes_status aes_server_submit(aes_server* s, const aes_request* req, uint64_t* ticket);
+
+/* Queues n requests at once (host array), all or none: AES_EAGAIN if fewer than n queue
+ * places are free, AES_EINVAL / AES_ENOMEM if any request is bad (nothing is queued then).
+ * tickets (host array of n) receives consecutive tickets in request order. */
+aes_status aes_server_submit_many(aes_server* s, const aes_request* reqs, size_t n, uint64_t* tickets);
+
+/* Waits up to timeout_us (0: do not wait; negative: no limit) for the ticket.  Returns AES_OK
+ * with *state = AES_REQ_DONE or AES_REQ_FAILED (the ticket is then released),
+ * AES_ETIMEDOUT with *state = AES_REQ_PENDING, or AES_ENOTFOUND for an unknown ticket. */
+aes_status aes_server_poll(aes_server* s, uint64_t ticket, int64_t timeout_us, int* state);
+
+aes_status aes_server_stats_get(aes_server* s, aes_server_stats* out);
+aes_status aes_server_stats_reset(aes_server* s);
+
+/* Fails every queued request, waits for the batches on the GPU, joins the thread and frees
+ * the server's memory.  NULL is a no-op. */
+aes_status aes_server_destroy(aes_server* s);
 
 #ifdef __cplusplus
 }

@@ -46,6 +46,47 @@ class aes_key_schedule(ctypes.Structure):
         return bytes(bytearray(self.rk))[: 16 * (self.nr + 1)]
 
 
+class aes_msg(ctypes.Structure):
+    _fields_ = [("key_idx", ctypes.c_uint32), ("dir", ctypes.c_uint32), ("offset", ctypes.c_uint64),
+                ("length", ctypes.c_uint64)]
+
+
+# numpy view of an aes_msg array (same layout, 24 bytes)
+def msg_dtype():
+    import numpy as np
+    return np.dtype([("key_idx", "<u4"), ("dir", "<u4"), ("offset", "<u8"), ("length", "<u8")])
+
+
+class aes_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32), ("nstreams", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("queue_capacity", ctypes.c_uint32), ("fail_every", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class aes_request(ctypes.Structure):
+    _fields_ = [("key_idx", ctypes.c_uint32), ("dir", ctypes.c_uint32), ("src", ctypes.c_void_p),
+                ("dst", ctypes.c_void_p), ("length", ctypes.c_uint64), ("src_on_device", ctypes.c_uint32),
+                ("dst_on_device", ctypes.c_uint32)]
+
+
+class aes_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "queued", "inflight", "launches",
+                                                "bytes_completed")] + \
+               [(n, ctypes.c_double) for n in ("p50_us", "p99_us", "max_us", "mean_us", "gbps", "mean_batch")]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+AES_REQ_PENDING, AES_REQ_DONE, AES_REQ_FAILED = 0, 1, 2
+
+
+def request_dtype():
+    """numpy view of aes_request (40 bytes)."""
+    import numpy as np
+    return np.dtype([("key_idx", "<u4"), ("dir", "<u4"), ("src", "<u8"), ("dst", "<u8"), ("length", "<u8"),
+                     ("src_on_device", "<u4"), ("dst_on_device", "<u4")])
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -59,6 +100,25 @@ _SIGS: dict[str, tuple] = {
     "aes_decrypt_blocks": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _VP]),
     "aes_crypt_blocks": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _I, _I, _VP]),
     "aes_crypt_host": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _I, _I, _VP]),
+    "aes_keypool_create": (_I, [_SZ, ctypes.POINTER(_VP)]),
+    "aes_keypool_load_keys": (_I, [_VP, ctypes.c_uint32, _SZ, _U8P, _I, _VP]),
+    "aes_keypool_set": (_I, [_VP, ctypes.c_uint32, _KSP]),
+    "aes_keypool_rounds": (_I, [_VP, ctypes.c_uint32]),
+    "aes_keypool_destroy": (_I, [_VP]),
+    "aes_batch_create": (_I, [_VP, _SZ, ctypes.POINTER(_VP)]),
+    "aes_batch_run": (_I, [_VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
+    "aes_batch_autotune": (_I, [_VP, _VP, _SZ, _VP, _VP, _SZ, ctypes.c_char_p, ctypes.POINTER(_I),
+                                ctypes.POINTER(_I), _VP]),
+    "aes_batch_set_shape": (_I, [_VP, _I, _I]),
+    "aes_batch_destroy": (_I, [_VP]),
+    "aes_crypt_batched": (_I, [_VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
+    "aes_server_create": (_I, [ctypes.POINTER(aes_server_cfg), _VP, ctypes.POINTER(_VP)]),
+    "aes_server_submit": (_I, [_VP, ctypes.POINTER(aes_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "aes_server_submit_many": (_I, [_VP, _VP, _SZ, _VP]),
+    "aes_server_poll": (_I, [_VP, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(_I)]),
+    "aes_server_stats_get": (_I, [_VP, ctypes.POINTER(aes_server_stats)]),
+    "aes_server_stats_reset": (_I, [_VP]),
+    "aes_server_destroy": (_I, [_VP]),
 }
 
 
@@ -74,6 +134,11 @@ def lib() -> ctypes.CDLL:
             f.restype, f.argtypes = res, args
         _lib = l
     return _lib
+
+
+def _dir(d) -> int:
+    """Direction name or number; unknown numbers pass through so the library rejects them."""
+    return _DIRS[d] if isinstance(d, str) else int(d)
 
 
 def declared_symbols() -> list[str]:
@@ -130,7 +195,7 @@ def aes_crypt_blocks(ks: aes_key_schedule, iv, d_in: int, d_out: int, nblocks: i
                      stream=None) -> None:
     ivp = _bytes_ptr(iv)
     _check(lib().aes_crypt_blocks(ctypes.byref(ks), ivp[0] if ivp else None, d_in, d_out, nblocks,
-                                  _DIRS[dir], _IMPLS[impl] if isinstance(impl, str) else int(impl),
+                                  _dir(dir), _IMPLS[impl] if isinstance(impl, str) else int(impl),
                                   _stream_ptr(stream)))
 
 
@@ -151,8 +216,159 @@ def aes_crypt_host(ks: aes_key_schedule, iv, h_in: int, h_out: int, nblocks: int
     """Host-buffer variant: h_in / h_out are host addresses; returns when h_out is written."""
     ivp = _bytes_ptr(iv)
     _check(lib().aes_crypt_host(ctypes.byref(ks), ivp[0] if ivp else None, h_in, h_out, nblocks,
-                                _DIRS[dir], _IMPLS[impl] if isinstance(impl, str) else int(impl),
+                                _dir(dir), _IMPLS[impl] if isinstance(impl, str) else int(impl),
                                 _stream_ptr(stream)))
+
+
+# ---- key pool and batches -------------------------------------------------------------------
+
+def _msgs_ptr(msgs):
+    """msgs: numpy array of msg_dtype() (or a list of (key_idx, dir, offset, length))."""
+    import numpy as np
+    a = np.ascontiguousarray(msgs if isinstance(msgs, np.ndarray) else np.array(msgs, dtype=msg_dtype()),
+                             dtype=msg_dtype())
+    return a, a.ctypes.data, a.shape[0]
+
+
+class KeyPool:
+    """Device-resident key schedules (aes_keypool_*)."""
+
+    def __init__(self, capacity: int):
+        h = _VP()
+        _check(lib().aes_keypool_create(capacity, ctypes.byref(h)))
+        self.handle = h
+        self.capacity = capacity
+
+    def load_keys(self, first: int, keys, key_bits: int, stream=None) -> None:
+        """Expand len(keys) raw keys (uint8 array, key_bits/8 bytes each) on the device."""
+        import numpy as np
+        k = np.ascontiguousarray(np.asarray(keys, dtype=np.uint8).reshape(-1))
+        count = k.size // (key_bits // 8)
+        _check(lib().aes_keypool_load_keys(self.handle, first, count, k.ctypes.data_as(_U8P), key_bits,
+                                           _stream_ptr(stream)))
+
+    def set(self, idx: int, ks: aes_key_schedule) -> None:
+        _check(lib().aes_keypool_set(self.handle, idx, ctypes.byref(ks)))
+
+    def rounds(self, idx: int) -> int:
+        return lib().aes_keypool_rounds(self.handle, idx)
+
+    def close(self) -> None:
+        if self.handle:
+            _check(lib().aes_keypool_destroy(self.handle))
+            self.handle = _VP()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """A reusable batched-launch context (aes_batch_*)."""
+
+    def __init__(self, pool: KeyPool, max_msgs: int):
+        h = _VP()
+        _check(lib().aes_batch_create(pool.handle, max_msgs, ctypes.byref(h)))
+        self.handle, self.pool = h, pool
+
+    def run(self, msgs, d_in: int, d_out: int, buf_bytes: int, stream=None) -> None:
+        a, p, n = _msgs_ptr(msgs)
+        _check(lib().aes_batch_run(self.handle, p, n, d_in, d_out, buf_bytes, _stream_ptr(stream)))
+
+    def autotune(self, msgs, d_in: int, d_out: int, buf_bytes: int, cache_path: str | None = None,
+                 stream=None) -> tuple[int, int]:
+        a, p, n = _msgs_ptr(msgs)
+        t, u = ctypes.c_int(), ctypes.c_int()
+        _check(lib().aes_batch_autotune(self.handle, p, n, d_in, d_out, buf_bytes,
+                                        cache_path.encode() if cache_path else None, ctypes.byref(t),
+                                        ctypes.byref(u), _stream_ptr(stream)))
+        return t.value, u.value
+
+    def set_shape(self, threads: int, blocks_per_lane: int) -> None:
+        _check(lib().aes_batch_set_shape(self.handle, threads, blocks_per_lane))
+
+    def close(self) -> None:
+        if self.handle:
+            _check(lib().aes_batch_destroy(self.handle))
+            self.handle = _VP()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def aes_crypt_batched(pool: KeyPool, msgs, d_in: int, d_out: int, buf_bytes: int, stream=None) -> None:
+    a, p, n = _msgs_ptr(msgs)
+    _check(lib().aes_crypt_batched(pool.handle, p, n, d_in, d_out, buf_bytes, _stream_ptr(stream)))
+
+
+# ---- server -----------------------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching request server (aes_server_*)."""
+
+    def __init__(self, pool: KeyPool, hbm_budget: int = 1 << 30, max_inflight: int = 1 << 16, nstreams: int = 4,
+                 max_batch: int = 4096, queue_capacity: int = 1 << 20, fail_every: int = 0):
+        cfg = aes_server_cfg(hbm_budget, max_inflight, nstreams, max_batch, queue_capacity, fail_every, 0)
+        h = _VP()
+        _check(lib().aes_server_create(ctypes.byref(cfg), pool.handle, ctypes.byref(h)))
+        self.handle, self.pool = h, pool
+
+    def submit(self, key_idx: int, dir, src: int, dst: int, length: int, src_on_device: bool,
+               dst_on_device: bool) -> int:
+        r = aes_request(key_idx, _dir(dir), src, dst, length, int(src_on_device), int(dst_on_device))
+        t = ctypes.c_uint64()
+        _check(lib().aes_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def submit_many(self, reqs) -> "np.ndarray":
+        """Queue a numpy array of request_dtype() all at once; returns the tickets (uint64)."""
+        import numpy as np
+        a = np.ascontiguousarray(reqs, dtype=request_dtype())
+        t = np.empty(a.shape[0], dtype=np.uint64)
+        _check(lib().aes_server_submit_many(self.handle, a.ctypes.data, a.shape[0], t.ctypes.data))
+        return t
+
+    def try_submit(self, *args, **kw) -> int | None:
+        """submit(), or None when the queue is full (AES_EAGAIN)."""
+        try:
+            return self.submit(*args, **kw)
+        except AesError as e:
+            if e.status == AES_EAGAIN:
+                return None
+            raise
+
+    def poll(self, ticket: int, timeout_us: int = -1) -> int:
+        """AES_REQ_DONE / AES_REQ_FAILED, or AES_REQ_PENDING when the wait ran out."""
+        st = ctypes.c_int()
+        rc = lib().aes_server_poll(self.handle, ticket, timeout_us, ctypes.byref(st))
+        if rc == AES_ETIMEDOUT:
+            return AES_REQ_PENDING
+        _check(rc)
+        return st.value
+
+    def stats(self) -> dict:
+        out = aes_server_stats()
+        _check(lib().aes_server_stats_get(self.handle, ctypes.byref(out)))
+        return out.as_dict()
+
+    def reset_stats(self) -> None:
+        _check(lib().aes_server_stats_reset(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            _check(lib().aes_server_destroy(self.handle))
+            self.handle = _VP()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # ---- torch conveniences (still one C call each) -------------------------------------------

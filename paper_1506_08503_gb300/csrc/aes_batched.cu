@@ -1,0 +1,484 @@
+// aes_batched.cu -- host side of the batched launch: descriptor staging, the cached CUDA
+// graph that replays [descriptor copy -> encrypt kernel -> decrypt kernel], the autotuner
+// and aes_crypt_batched.
+//
+// Per run the host splits the messages by direction, drops empty ones, writes 32-byte
+// descriptors plus each message's first block in the direction's concatenated block space
+// into pinned staging, copies them to the device on the batch's own copy stream (so the
+// upload overlaps whatever the caller's stream is still running, e.g. the previous batch),
+// and launches the graph [encrypt kernel -> decrypt kernel] on the caller's stream behind that
+// copy.  The graph is built once per (buffer, shape); later runs only patch the kernel
+// arguments (cudaGraphExecKernelNodeSetParams) when they change and switch off a direction
+// without work.  Two staging/device buffer pairs alternate; a run waits for the run that used
+// its pair two calls ago, so descriptors are never overwritten while a kernel reads them.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <mutex>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "aes_internal.cuh"
+
+namespace {
+
+using namespace aesgb;
+
+constexpr size_t kMaxMsgs = size_t(1) << 24;
+
+struct Shape {
+  int threads, bpl;
+};
+// (CTA threads, blocks each lane enciphers per window)
+constexpr Shape kShapes[] = {{512, 1}, {512, 2}, {512, 4}, {384, 4}, {256, 4}};
+
+struct Slot {
+  uint8_t* host = nullptr;  // pinned staging
+  uint8_t* dev = nullptr;
+  cudaEvent_t done = nullptr;    // the kernels that read this slot have finished
+  cudaEvent_t copied = nullptr;  // this slot's descriptors are on the device
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t kenc = nullptr, kdec = nullptr;
+  int g_threads = 0, g_bpl = 0;
+  // what the instantiated graph currently holds, to skip redundant updates
+  unsigned g_grid[2] = {0, 0};
+  BatchDir g_bd[2] = {};
+  uint64_t g_in = 0, g_out = 0;
+  int g_enabled[2] = {-1, -1};
+};
+
+struct Layout {
+  size_t enc_msgs, dec_msgs, enc_start, dec_start, end;
+};
+
+Layout layout(size_t nenc, size_t ndec) {
+  Layout l;
+  l.enc_msgs = 0;
+  l.dec_msgs = l.enc_msgs + nenc * sizeof(BatchMsg);
+  l.enc_start = l.dec_msgs + ndec * sizeof(BatchMsg);
+  l.dec_start = l.enc_start + (nenc + 1) * sizeof(uint64_t);
+  l.end = l.dec_start + (ndec + 1) * sizeof(uint64_t);
+  return l;
+}
+
+}  // namespace
+
+struct aes_batch {
+  aes_keypool* pool = nullptr;
+  int device = -1;
+  size_t max_msgs = 0;
+  size_t bytes = 0;
+  int threads = 512, bpl = 2;
+  Slot slot[2];
+  int next = 0;
+  cudaStream_t copy_stream = nullptr;
+  std::mutex mu;
+};
+
+namespace {
+
+void free_slot(Slot& s) {
+  if (s.exec) cudaGraphExecDestroy(s.exec);
+  if (s.graph) cudaGraphDestroy(s.graph);
+  if (s.done) cudaEventDestroy(s.done);
+  if (s.copied) cudaEventDestroy(s.copied);
+  if (s.dev) cudaFree(s.dev);
+  if (s.host) cudaFreeHost(s.host);
+  s = Slot{};
+}
+
+struct KernelArgs {
+  uint64_t in;
+  uint64_t out;
+  BatchDir bd;
+  const PoolEntry* pool;
+  void* ptrs[4];
+  void fix() {
+    ptrs[0] = &in;
+    ptrs[1] = &out;
+    ptrs[2] = &bd;
+    ptrs[3] = &pool;
+  }
+};
+
+cudaKernelNodeParams kernel_params(TTBatchedFn fn, unsigned grid, int threads, size_t smem, KernelArgs& a) {
+  a.fix();
+  cudaKernelNodeParams p{};
+  p.func = reinterpret_cast<void*>(fn);
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(unsigned(threads));
+  p.sharedMemBytes = unsigned(smem);
+  p.kernelParams = a.ptrs;
+  p.extra = nullptr;
+  return p;
+}
+
+aes_status build_graph(aes_batch* b, Slot& s, const cudaKernelNodeParams& pe, const cudaKernelNodeParams& pd) {
+  if (s.exec) { cudaGraphExecDestroy(s.exec); s.exec = nullptr; }
+  if (s.graph) { cudaGraphDestroy(s.graph); s.graph = nullptr; }
+  cudaError_t e;
+  if ((e = cudaGraphCreate(&s.graph, 0)) != cudaSuccess) return cuda_error(e, "cudaGraphCreate");
+  if ((e = cudaGraphAddKernelNode(&s.kenc, s.graph, nullptr, 0, &pe)) != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode(enc)");
+  if ((e = cudaGraphAddKernelNode(&s.kdec, s.graph, &s.kenc, 1, &pd)) != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode(dec)");
+  if ((e = cudaGraphInstantiate(&s.exec, s.graph, 0)) != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+  s.g_threads = b->threads;
+  s.g_bpl = b->bpl;
+  s.g_enabled[0] = s.g_enabled[1] = -1;
+  return AES_OK;
+}
+
+bool same_dir(const BatchDir& a, const BatchDir& b) {
+  return a.msgs == b.msgs && a.start == b.start && a.total == b.total && a.nmsgs == b.nmsgs;
+}
+
+// The kernels' dynamic shared-memory limit is raised once per device and kernel.
+aes_status ensure_smem_attr(TTBatchedFn f, size_t smem) {
+  static std::mutex mu;
+  static std::vector<std::pair<int, const void*>> done;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(mu);
+  for (const auto& d : done)
+    if (d.first == dev && d.second == reinterpret_cast<const void*>(f)) return AES_OK;
+  if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
+    return cuda_error(e, "cudaFuncSetAttribute(batched)");
+  done.emplace_back(dev, reinterpret_cast<const void*>(f));
+  return AES_OK;
+}
+
+}  // namespace
+
+namespace aesgb {
+
+// Writes nenc + ndec descriptors through `fill` into the next staging slot, computes the
+// per-direction block starts and launches the graph on `stream`.  Caller holds b->mu.
+aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
+                              const std::function<void(BatchMsg*, BatchMsg*)>& fill, uint64_t in_base,
+                              uint64_t out_base, cudaStream_t stream) {
+  cudaError_t e;
+  if (nenc + ndec > b->max_msgs) return set_error(AES_EINVAL, "%zu messages exceed the batch capacity %zu", nenc + ndec, b->max_msgs);
+  Slot& s = b->slot[b->next];
+  b->next ^= 1;
+  if ((e = cudaEventSynchronize(s.done)) != cudaSuccess) return cuda_error(e, "waiting for a previous batch");
+  const Layout L = layout(nenc, ndec);
+  uint8_t* h = s.host;
+  BatchMsg* em = reinterpret_cast<BatchMsg*>(h + L.enc_msgs);
+  BatchMsg* dm = reinterpret_cast<BatchMsg*>(h + L.dec_msgs);
+  uint64_t* es = reinterpret_cast<uint64_t*>(h + L.enc_start);
+  uint64_t* ds = reinterpret_cast<uint64_t*>(h + L.dec_start);
+  fill(em, dm);
+  uint64_t te = 0, td = 0;
+  for (size_t i = 0; i < nenc; ++i) { es[i] = te; te += em[i].nblocks; }
+  for (size_t i = 0; i < ndec; ++i) { ds[i] = td; td += dm[i].nblocks; }
+  es[nenc] = te;
+  ds[ndec] = td;
+
+  const DeviceInfo* di = current_device_info();
+  if (!di) return AES_ECUDA;
+  TTBatchedFn fe = ttable_batched_enc(b->threads, b->bpl), fd = ttable_batched_dec(b->threads, b->bpl);
+  if (!fe || !fd) return set_error(AES_EINVAL, "shape (%d threads, %d blocks per lane) is not compiled", b->threads, b->bpl);
+  const size_t se = ttable_smem_bytes(AES_ENCRYPT), sd = ttable_smem_bytes(AES_DECRYPT);
+  aes_status ast = ensure_smem_attr(fe, se);
+  if (ast == AES_OK) ast = ensure_smem_attr(fd, sd);
+  if (ast != AES_OK) return ast;
+  KernelArgs ae{in_base, out_base,
+                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.enc_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.enc_start),
+                         te, uint32_t(nenc), 0u},
+                b->pool->entries, {}};
+  KernelArgs ad{in_base, out_base,
+                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.dec_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.dec_start),
+                         td, uint32_t(ndec), 0u},
+                b->pool->entries, {}};
+  // one CTA per SM (fewer when a direction has less than one block per thread)
+  const uint64_t per_cta = uint64_t(b->threads);
+  const unsigned ge = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(di->sms, (te + per_cta - 1) / per_cta)));
+  const unsigned gd = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(di->sms, (td + per_cta - 1) / per_cta)));
+  const cudaKernelNodeParams pe = kernel_params(fe, ge, b->threads, se, ae);
+  const cudaKernelNodeParams pd = kernel_params(fd, gd, b->threads, sd, ad);
+  if (!s.exec || s.g_threads != b->threads || s.g_bpl != b->bpl) {
+    aes_status st = build_graph(b, s, pe, pd);
+    if (st != AES_OK) return st;
+  } else {
+    const bool same_io = s.g_in == in_base && s.g_out == out_base;
+    if (!(same_io && s.g_grid[0] == ge && same_dir(s.g_bd[0], ae.bd)))
+      if ((e = cudaGraphExecKernelNodeSetParams(s.exec, s.kenc, &pe)) != cudaSuccess) return cuda_error(e, "cudaGraphExecKernelNodeSetParams(enc)");
+    if (!(same_io && s.g_grid[1] == gd && same_dir(s.g_bd[1], ad.bd)))
+      if ((e = cudaGraphExecKernelNodeSetParams(s.exec, s.kdec, &pd)) != cudaSuccess) return cuda_error(e, "cudaGraphExecKernelNodeSetParams(dec)");
+  }
+  s.g_in = in_base;
+  s.g_out = out_base;
+  s.g_grid[0] = ge;
+  s.g_grid[1] = gd;
+  s.g_bd[0] = ae.bd;
+  s.g_bd[1] = ad.bd;
+  // a direction without work is switched off in the instantiated graph (no empty launch)
+  const int en_e = te ? 1 : 0, en_d = td ? 1 : 0;
+  if (s.g_enabled[0] != en_e) {
+    if ((e = cudaGraphNodeSetEnabled(s.exec, s.kenc, unsigned(en_e))) != cudaSuccess) return cuda_error(e, "cudaGraphNodeSetEnabled");
+    s.g_enabled[0] = en_e;
+  }
+  if (s.g_enabled[1] != en_d) {
+    if ((e = cudaGraphNodeSetEnabled(s.exec, s.kdec, unsigned(en_d))) != cudaSuccess) return cuda_error(e, "cudaGraphNodeSetEnabled");
+    s.g_enabled[1] = en_d;
+  }
+  if ((e = cudaMemcpyAsync(s.dev, s.host, L.end, cudaMemcpyHostToDevice, b->copy_stream)) != cudaSuccess)
+    return cuda_error(e, "descriptor upload");
+  if ((e = cudaEventRecord(s.copied, b->copy_stream)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+  if ((e = cudaStreamWaitEvent(stream, s.copied, 0)) != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
+  if ((e = cudaGraphLaunch(s.exec, stream)) != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
+  if ((e = cudaEventRecord(s.done, stream)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+  return AES_OK;
+}
+
+}  // namespace aesgb
+
+namespace {
+
+aes_status run_locked(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const void* d_in, void* d_out,
+                      size_t buf_bytes, cudaStream_t stream) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  if (dev != b->device) return set_error(AES_EINVAL, "batch belongs to device %d, current device is %d", b->device, dev);
+  if (nmsgs > b->max_msgs) return set_error(AES_EINVAL, "%zu messages exceed the batch capacity %zu", nmsgs, b->max_msgs);
+  if (nmsgs && !msgs) return set_error(AES_EINVAL, "null message array");
+  if ((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 15u)
+    return set_error(AES_EINVAL, "buffers must be 16-byte aligned");
+  const uintptr_t a = reinterpret_cast<uintptr_t>(d_in), o = reinterpret_cast<uintptr_t>(d_out);
+  if (a != o && a < o + buf_bytes && o < a + buf_bytes)
+    return set_error(AES_EINVAL, "input and output overlap without being identical");
+  const aes_keypool* pool = b->pool;
+  size_t nenc = 0, ndec = 0;
+  for (size_t i = 0; i < nmsgs; ++i) {
+    const aes_msg& m = msgs[i];
+    if (m.dir != AES_ENCRYPT && m.dir != AES_DECRYPT) return set_error(AES_EINVAL, "message %zu: bad dir %u", i, m.dir);
+    if ((m.offset | m.length) & 15u) return set_error(AES_EINVAL, "message %zu: offset and length must be multiples of 16", i);
+    if (m.offset > buf_bytes || m.length > buf_bytes - m.offset)
+      return set_error(AES_EINVAL, "message %zu: [%llu, +%llu) leaves the %zu-byte buffers", i,
+                       (unsigned long long)m.offset, (unsigned long long)m.length, buf_bytes);
+    if (m.length == 0) continue;
+    if (!d_in || !d_out) return set_error(AES_EINVAL, "null buffer");
+    if (size_t(m.key_idx) >= pool->capacity || pool->nr[m.key_idx] == 0)
+      return set_error(AES_EINVAL, "message %zu: key slot %u is not loaded", i, m.key_idx);
+    (m.dir == AES_ENCRYPT ? nenc : ndec)++;
+  }
+  auto fill = [&](BatchMsg* em, BatchMsg* dm) {
+    size_t ie = 0, id = 0;
+    for (size_t i = 0; i < nmsgs; ++i) {
+      const aes_msg& m = msgs[i];
+      if (m.length == 0) continue;
+      const BatchMsg d{m.key_idx, 0u, m.offset / 16, m.offset / 16, m.length / 16};
+      if (m.dir == AES_ENCRYPT) em[ie++] = d;
+      else dm[id++] = d;
+    }
+  };
+  return batch_launch_descs(b, nenc, ndec, fill, reinterpret_cast<uint64_t>(d_in), reinterpret_cast<uint64_t>(d_out), stream);
+}
+
+bool shape_compiled(int threads, int bpl) {
+  for (const Shape& sh : kShapes)
+    if (sh.threads == threads && sh.bpl == bpl) return true;
+  return false;
+}
+
+// ---- autotune cache: a flat JSON object {"signature": {"threads": T, "blocks_per_lane": U, "us": x}, ...}
+std::string read_file(const char* path) {
+  std::string out;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return out;
+  char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) out.append(buf, n);
+  std::fclose(f);
+  return out;
+}
+
+bool cache_lookup(const std::string& text, const std::string& sig, int* threads, int* bpl) {
+  const std::string key = "\"" + sig + "\"";
+  size_t p = text.find(key);
+  if (p == std::string::npos) return false;
+  int t = 0, u = 0;
+  const size_t pt = text.find("\"threads\":", p), pu = text.find("\"blocks_per_lane\":", p);
+  if (pt == std::string::npos || pu == std::string::npos) return false;
+  if (std::sscanf(text.c_str() + pt + 10, "%d", &t) != 1 || std::sscanf(text.c_str() + pu + 18, "%d", &u) != 1) return false;
+  if (!shape_compiled(t, u)) return false;
+  *threads = t;
+  *bpl = u;
+  return true;
+}
+
+void cache_store(const char* path, const std::string& text, const std::string& sig, int threads, int bpl, double us) {
+  char entry[512];
+  std::snprintf(entry, sizeof(entry), "\"%s\": {\"threads\": %d, \"blocks_per_lane\": %d, \"us\": %.1f}", sig.c_str(), threads, bpl, us);
+  std::string body = text;
+  const size_t close = body.rfind('}');
+  if (body.empty() || close == std::string::npos || body.find('{') == std::string::npos) body = std::string("{\n  ") + entry + "\n}\n";
+  else {
+    const bool empty = body.find('"') == std::string::npos;
+    body = body.substr(0, close);
+    while (!body.empty() && (body.back() == '\n' || body.back() == ' ')) body.pop_back();
+    body += (empty ? "\n  " : ",\n  ") + std::string(entry) + "\n}\n";
+  }
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  std::fwrite(body.data(), 1, body.size(), f);
+  std::fclose(f);
+  std::rename(tmp.c_str(), path);
+}
+
+std::string signature(const DeviceInfo* di, const aes_msg* msgs, size_t n) {
+  uint64_t blocks = 0, enc = 0;
+  for (size_t i = 0; i < n; ++i) {
+    blocks += msgs[i].length / 16;
+    if (msgs[i].dir == AES_ENCRYPT) enc += msgs[i].length / 16;
+  }
+  // bucket sizes to powers of two so that nearby workloads share an entry
+  auto lg = [](uint64_t v) { int b = 0; while (v > 1) { v >>= 1; ++b; } return b; };
+  char buf[400];
+  std::snprintf(buf, sizeof(buf), "%s|msgs=2^%d|blocks=2^%d|enc=%d%%", di->name, lg(n), lg(blocks),
+                blocks ? int(100 * enc / blocks) : 0);
+  return buf;
+}
+
+}  // namespace
+
+using namespace aesgb;
+
+extern "C" {
+
+aes_status aes_batch_destroy(aes_batch* b) {
+  clear_error();
+  if (!b) return AES_OK;
+  for (Slot& s : b->slot) {
+    if (s.done) cudaEventSynchronize(s.done);
+    free_slot(s);
+  }
+  if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
+  delete b;
+  return AES_OK;
+}
+
+aes_status aes_batch_create(aes_keypool* pool, size_t max_msgs, aes_batch** out) {
+  clear_error();
+  if (!out) return set_error(AES_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!pool || !pool->entries) return set_error(AES_EINVAL, "null key pool");
+  if (max_msgs == 0 || max_msgs > kMaxMsgs) return set_error(AES_EINVAL, "max_msgs must be 1..2^24 (got %zu)", max_msgs);
+  aes_batch* b = new (std::nothrow) aes_batch();
+  if (!b) return set_error(AES_ENOMEM, "host allocation failed");
+  b->pool = pool;
+  b->max_msgs = max_msgs;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e != cudaSuccess) { delete b; return cuda_error(e, "cudaGetDevice"); }
+  if (b->device != pool->device) { delete b; return set_error(AES_EINVAL, "pool and batch on different devices"); }
+  b->bytes = layout(max_msgs, max_msgs).end;  // enough for any split of max_msgs
+  if ((e = cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    delete b;
+    return cuda_error(e, "cudaStreamCreate");
+  }
+  for (Slot& s : b->slot) {
+    if ((e = cudaMallocHost(&s.host, b->bytes)) != cudaSuccess || (e = cudaMalloc(&s.dev, b->bytes)) != cudaSuccess) {
+      aes_batch_destroy(b);
+      return set_error(AES_ENOMEM, "batch buffers (%zu bytes) could not be allocated: %s", b->bytes, cudaGetErrorString(e));
+    }
+    if ((e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming)) != cudaSuccess) {
+      aes_batch_destroy(b);
+      return cuda_error(e, "cudaEventCreate");
+    }
+  }
+  *out = b;
+  return AES_OK;
+}
+
+aes_status aes_batch_run(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const void* d_in, void* d_out,
+                         size_t buf_bytes, void* cuda_stream) {
+  clear_error();
+  if (!b) return set_error(AES_EINVAL, "null batch");
+  std::lock_guard<std::mutex> lk(b->mu);
+  return run_locked(b, msgs, nmsgs, d_in, d_out, buf_bytes, static_cast<cudaStream_t>(cuda_stream));
+}
+
+aes_status aes_batch_set_shape(aes_batch* b, int threads, int blocks_per_lane) {
+  clear_error();
+  if (!b) return set_error(AES_EINVAL, "null batch");
+  if (!shape_compiled(threads, blocks_per_lane))
+    return set_error(AES_EINVAL, "shape (%d threads, %d blocks per lane) is not compiled", threads, blocks_per_lane);
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->threads = threads;
+  b->bpl = blocks_per_lane;
+  return AES_OK;
+}
+
+aes_status aes_batch_autotune(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const void* d_in, void* d_out,
+                              size_t buf_bytes, const char* cache_path, int* threads, int* blocks_per_lane,
+                              void* cuda_stream) {
+  clear_error();
+  if (!b) return set_error(AES_EINVAL, "null batch");
+  const DeviceInfo* di = current_device_info();
+  if (!di) return AES_ECUDA;
+  std::lock_guard<std::mutex> lk(b->mu);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const std::string sig = signature(di, msgs, nmsgs);
+  std::string text = cache_path ? read_file(cache_path) : std::string();
+  int t = 0, u = 0;
+  if (cache_path && cache_lookup(text, sig, &t, &u)) {
+    b->threads = t;
+    b->bpl = u;
+  } else {
+    cudaEvent_t e0, e1;
+    cudaError_t ce;
+    if ((ce = cudaEventCreate(&e0)) != cudaSuccess || (ce = cudaEventCreate(&e1)) != cudaSuccess) return cuda_error(ce, "cudaEventCreate");
+    double best = 1e30;
+    Shape best_shape = kShapes[0];
+    aes_status result = AES_OK;
+    for (const Shape& sh : kShapes) {
+      b->threads = sh.threads;
+      b->bpl = sh.bpl;
+      if ((result = run_locked(b, msgs, nmsgs, d_in, d_out, buf_bytes, st)) != AES_OK) break;  // warm-up, builds the graph
+      if ((result = run_locked(b, msgs, nmsgs, d_in, d_out, buf_bytes, st)) != AES_OK) break;  // graph for the other slot
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 3 && result == AES_OK; ++rep) {
+        cudaEventRecord(e0, st);
+        result = run_locked(b, msgs, nmsgs, d_in, d_out, buf_bytes, st);
+        cudaEventRecord(e1, st);
+        if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) { result = cuda_error(ce, "autotune timing"); break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_min = std::min(ms_min, ms);
+      }
+      if (result != AES_OK) break;
+      if (ms_min < best) { best = ms_min; best_shape = sh; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != AES_OK) return result;
+    b->threads = best_shape.threads;
+    b->bpl = best_shape.bpl;
+    if (cache_path) cache_store(cache_path, text, sig, b->threads, b->bpl, best * 1e3);
+  }
+  if (threads) *threads = b->threads;
+  if (blocks_per_lane) *blocks_per_lane = b->bpl;
+  return AES_OK;
+}
+
+aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsgs, const void* d_in,
+                             void* d_out, size_t buf_bytes, void* cuda_stream) {
+  clear_error();
+  if (!pool || !pool->entries || !pool->mu) return set_error(AES_EINVAL, "null key pool");
+  std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(pool->mu));
+  if (!pool->internal || pool->internal->max_msgs < nmsgs) {
+    if (pool->internal) { aes_batch_destroy(pool->internal); pool->internal = nullptr; }
+    aes_status st = aes_batch_create(pool, std::max<size_t>(nmsgs, 1024), &pool->internal);
+    if (st != AES_OK) return st;
+  }
+  return aes_batch_run(pool->internal, msgs, nmsgs, d_in, d_out, buf_bytes, cuda_stream);
+}
+
+}  // extern "C"

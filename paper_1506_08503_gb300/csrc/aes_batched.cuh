@@ -1,0 +1,167 @@
+// aes_batched.cuh -- persistent T-table kernel over many messages, each with its own key.
+//
+// The paper keeps one key schedule per message (the tensor K, Section II) and processes all
+// messages of a matrix together.  Here the messages of one direction are laid end to end in a
+// virtual block space of G blocks (message m covers [start[m], start[m+1])), and that space
+// is cut into one equal contiguous slice per warp, so every warp gets the same amount of work
+// whatever the length distribution, without atomics or per-tile searches.  Round keys sit in
+// registers and are reloaded from the device key pool only when the key changes.  AES-128,
+// -192 and -256 messages can share a launch: the round count is read with the key.
+#pragma once
+#include "aes_ttable.cuh"
+
+namespace aesgb {
+namespace tt {
+
+struct Cursor {
+  uint32_t m = 0;
+  uint64_t start = 0, end = 0, src = 0, dst = 0;
+  uint32_t key = 0xFFFFFFFFu;
+};
+
+__device__ __forceinline__ uint64_t ldg64(const uint64_t* p) {
+  return __ldg(reinterpret_cast<const unsigned long long*>(p));
+}
+
+// Message m with start[m] <= g < start[m + 1] (start strictly increasing, start[0] = 0).
+__device__ __forceinline__ uint32_t find_msg(const uint64_t* start, uint32_t nmsgs, uint64_t g) {
+  uint32_t lo = 0, hi = nmsgs;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (ldg64(start + mid) <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void open_msg(Cursor& c, const BatchDir& bd, uint32_t m) {
+  c.m = m;
+  c.start = ldg64(bd.start + m);
+  c.end = ldg64(bd.start + m + 1);
+  c.src = ldg64(&bd.msgs[m].src_block);
+  c.dst = ldg64(&bd.msgs[m].dst_block);
+  c.key = __ldg(&bd.msgs[m].key_idx);
+}
+
+// Moves the cursor forward until it holds block g (g below the direction's total).
+__device__ __forceinline__ void seek(Cursor& c, const BatchDir& bd, uint64_t g) {
+  while (g >= c.end) open_msg(c, bd, c.m + 1);
+}
+
+template <int DIR>
+__device__ __forceinline__ void load_key(const PoolEntry* pool, uint32_t key, uint32_t (&kw)[kMaxRounds + 1][4],
+                                         uint32_t (&kl)[4], int& nr) {
+  const PoolEntry* e = pool + key;
+  const uint4* kp = reinterpret_cast<const uint4*>(DIR == AES_ENCRYPT ? &e->enc[0][0] : &e->dec[0][0]);
+#pragma unroll
+  for (int r = 0; r < kMaxRounds; ++r) {
+    const uint4 q = __ldg(kp + r);
+    kw[r][0] = q.x; kw[r][1] = q.y; kw[r][2] = q.z; kw[r][3] = q.w;
+  }
+  nr = __ldg(&e->nr);
+  const uint4 q = __ldg(kp + nr);
+  kl[0] = q.x; kl[1] = q.y; kl[2] = q.z; kl[3] = q.w;
+}
+
+// Rounds 1..nr-1 of one block with the round keys in registers (nr = 10, 12 or 14; the
+// branches are warp-uniform on the fast path).
+template <int DIR>
+__device__ __forceinline__ uint4 crypt_rt(uint4 v, const uint32_t (&kw)[kMaxRounds + 1][4], const uint32_t (&kl)[4],
+                                          int nr, const char* sm, uint32_t lc) {
+  uint32_t s0 = v.x ^ kw[0][0], s1 = v.y ^ kw[0][1], s2 = v.z ^ kw[0][2], s3 = v.w ^ kw[0][3];
+#pragma unroll
+  for (int r = 1; r < 10; ++r) tt_round<DIR>(s0, s1, s2, s3, kw[r][0], kw[r][1], kw[r][2], kw[r][3], sm, lc);
+  if (nr > 10) {
+#pragma unroll
+    for (int r = 10; r < 12; ++r) tt_round<DIR>(s0, s1, s2, s3, kw[r][0], kw[r][1], kw[r][2], kw[r][3], sm, lc);
+    if (nr > 12) {
+#pragma unroll
+      for (int r = 12; r < 14; ++r) tt_round<DIR>(s0, s1, s2, s3, kw[r][0], kw[r][1], kw[r][2], kw[r][3], sm, lc);
+    }
+  }
+  return tt_final<DIR>(s0, s1, s2, s3, kl[0], kl[1], kl[2], kl[3], sm, lc);
+}
+
+// Warps step through their slice in windows of up to 32 * U blocks (lane l takes blocks
+// base + l + 32u) that never cross a message boundary: a window ends where its message ends.
+// The key, the round count and the source/destination bases are therefore the same for the
+// whole warp (uniform registers and branches), and each lane enciphers U independent blocks.
+// A window cut short by a message end leaves lanes idle; over lognormal lengths (median 4 KiB)
+// that costs a few percent, less than per-lane keys at the boundaries would.  The next window
+// of the same message is prefetched into L2 while the current one is enciphered.
+template <int DIR, int THREADS, int U>
+__global__ void __launch_bounds__(THREADS, 1)
+tt_batched_kernel(uint64_t in_base, uint64_t out_base, const BatchDir bd, const PoolEntry* pool) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  if (bd.total == 0) return;  // grid-uniform, before any barrier
+  fill_tables<DIR>(smem);
+  __syncthreads();
+  const char* sm = reinterpret_cast<const char*>(smem);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lc = lane * 4u;
+  const uint64_t nwarps = uint64_t(gridDim.x) * (THREADS / 32);
+  const uint64_t w = (uint64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5;
+  const uint64_t hi = bd.total * (w + 1) / nwarps;
+  uint64_t gb = bd.total * w / nwarps;
+  if (gb >= hi) return;  // warp-uniform; no barrier follows
+
+  uint32_t kw[kMaxRounds + 1][4];
+  uint32_t kl[4];
+  int nr = 0;
+  Cursor c;  // warp-uniform: the message holding block gb
+  open_msg(c, bd, find_msg(bd.start, bd.nmsgs, gb));
+  load_key<DIR>(pool, c.key, kw, kl, nr);
+  constexpr uint32_t kWin = 32u * U;
+
+  while (gb < hi) {
+    if (gb >= c.end) {
+      const uint32_t old = c.key;
+      seek(c, bd, gb);
+      if (c.key != old) load_key<DIR>(pool, c.key, kw, kl, nr);
+    }
+    uint64_t wend = gb + kWin;
+    if (wend > hi) wend = hi;
+    if (wend > c.end) wend = c.end;
+    const uint4* src = reinterpret_cast<const uint4*>(in_base + (c.src + (gb - c.start)) * 16u);
+    uint4* dst = reinterpret_cast<uint4*>(out_base + (c.dst + (gb - c.start)) * 16u);
+    const uint32_t cnt = uint32_t(wend - gb);
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t i = u * 32u + lane;
+      v[u] = i < cnt ? ld_block(src + i) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    // the next window of the same message goes to L2 while this one is enciphered
+    uint64_t nend = wend + kWin;
+    if (nend > hi) nend = hi;
+    if (nend > c.end) nend = c.end;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = kWin + u * 32u + lane;
+      if (gb + i < nend) prefetch_l2(src + i);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = crypt_rt<DIR>(v[u], kw, kl, nr, sm, lc);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t i = u * 32u + lane;
+      if (i < cnt) st_block(dst + i, v[u]);
+    }
+    gb = wend;
+  }
+}
+
+// Compiled shapes the autotuner may pick: (CTA threads, blocks per lane per window).  One
+// CTA per SM: the tables take 128-192 KiB of shared memory.
+template <int DIR>
+TTBatchedFn select_batched(int threads, int u) {
+  if (threads == 512 && u == 1) return tt_batched_kernel<DIR, 512, 1>;
+  if (threads == 512 && u == 2) return tt_batched_kernel<DIR, 512, 2>;
+  if (threads == 512 && u == 4) return tt_batched_kernel<DIR, 512, 4>;
+  if (threads == 384 && u == 4) return tt_batched_kernel<DIR, 384, 4>;
+  if (threads == 256 && u == 4) return tt_batched_kernel<DIR, 256, 4>;
+  return nullptr;
+}
+
+}  // namespace tt
+}  // namespace aesgb

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 
 #include "aes_field.cuh"
 #include "aesgb.h"
@@ -70,4 +71,63 @@ aes_status launch_bitslice(int dir, const aes_key_schedule& ks, const uint8_t* i
 // Shared-memory bytes one T-table CTA needs for direction `dir`.
 size_t ttable_smem_bytes(int dir);
 
+// ---- key pool ------------------------------------------------------------------------------
+// One device-resident key: the encryption words and the equivalent-inverse-cipher words
+// (InvMixColumns applied to the middle round keys), both in round order.  512 bytes.
+struct PoolEntry {
+  uint32_t enc[kMaxRounds + 1][4];
+  uint32_t dec[kMaxRounds + 1][4];
+  int32_t nr;
+  uint32_t pad[7];
+};
+static_assert(sizeof(PoolEntry) == 512, "pool entries are 512 bytes");
+
+// ---- batched messages ------------------------------------------------------------------------
+struct BatchMsg {
+  uint32_t key_idx;
+  uint32_t pad;
+  uint64_t src_block;  // first input block, counted from the input base address
+  uint64_t dst_block;  // first output block, counted from the output base address
+  uint64_t nblocks;
+};
+static_assert(sizeof(BatchMsg) == 32, "batch descriptors are 32 bytes");
+
+// Work of one direction: messages laid end to end; start[m] is the first block of message m
+// in that virtual block space (nmsgs + 1 entries, the last = total).
+struct BatchDir {
+  const BatchMsg* msgs;
+  const uint64_t* start;
+  uint64_t total;
+  uint32_t nmsgs;
+  uint32_t pad;
+};
+
+// Kernel arguments: input and output base addresses as integers (the server passes 0 and
+// absolute block numbers), the direction's work, the key pool.
+using TTBatchedFn = void (*)(uint64_t, uint64_t, const BatchDir, const PoolEntry*);
+// Compiled shapes (CTA threads, blocks per lane per window); nullptr if not compiled.
+TTBatchedFn ttable_batched_enc(int threads, int blocks_per_lane);
+TTBatchedFn ttable_batched_dec(int threads, int blocks_per_lane);
+
 }  // namespace aesgb
+
+struct aes_batch;
+
+namespace aesgb {
+// Launches one batch from descriptors written by `fill(enc, dec)` (nenc and ndec entries,
+// nblocks > 0 each) relative to in_base / out_base.  The caller holds the batch's lock.
+aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
+                              const std::function<void(BatchMsg*, BatchMsg*)>& fill, uint64_t in_base,
+                              uint64_t out_base, cudaStream_t stream);
+}  // namespace aesgb
+
+struct aes_keypool {
+  int device = -1;
+  size_t capacity = 0;
+  aesgb::PoolEntry* entries = nullptr;  // device
+  uint8_t* raw = nullptr;               // device staging for raw keys
+  size_t raw_cap = 0;                   // bytes
+  int8_t* nr = nullptr;                 // host shadow: rounds per slot (0 = empty)
+  aes_batch* internal = nullptr;        // for aes_crypt_batched
+  void* mu = nullptr;                   // std::mutex*, serialises aes_crypt_batched
+};

@@ -1,0 +1,515 @@
+// aes_server.cu -- request server with continuous batching over the batched T-table launch.
+//
+// The paper's point (Sections III-IV) is throughput on many small messages by processing
+// them together; a server adds the time dimension: requests arrive one by one.  The server's
+// thread keeps a FIFO of submitted requests and, whenever one of its CUDA streams is idle,
+// admits as many queued requests as the in-flight limit, the batch size and the free staging
+// memory allow, and starts them as ONE batched launch on that stream:
+//   host-sourced payloads are copied into the staging arena (or straight into a device
+//   destination), the batch graph runs the cipher in place or device-to-device, and host
+//   destinations are copied back; a host callback at the end of the stream marks the batch
+//   complete and wakes the thread.
+// Requests arriving while batches run are admitted into the next free stream's batch, so the
+// device works on several batches at once and nobody waits for a full drain.
+//
+// Staging memory is one cudaMalloc'd arena (the HBM budget) managed by a first-fit free list
+// with coalescing; a request is admitted only when its staging fits (head-of-line order is
+// kept, so large requests are not starved by small ones).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "aes_internal.cuh"
+
+namespace {
+
+using namespace aesgb;
+using Clock = std::chrono::steady_clock;
+
+double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
+
+// First-fit allocator over [0, size) with 256-byte granularity and coalescing frees.
+class Arena {
+ public:
+  explicit Arena(size_t size = 0) { reset(size); }
+  void reset(size_t size) {
+    free_.clear();
+    if (size) free_[0] = size;
+    size_ = size;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = (bytes + 255) & ~size_t(255);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes, start = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + bytes == next->first) {
+      bytes += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += bytes;
+        return;
+      }
+    }
+    free_[off] = bytes;
+  }
+  size_t largest_possible() const { return size_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t size_ = 0;
+};
+
+struct Req {
+  aes_request r{};
+  double t_submit = 0, t_done = 0;
+  int state = AES_REQ_PENDING;
+  bool staged = false;
+  size_t stage_off = 0, stage_bytes = 0;
+};
+
+struct StreamSlot {
+  cudaStream_t stream = nullptr;
+  aes_batch* batch = nullptr;
+  bool busy = false;
+  std::vector<uint64_t> tickets;
+};
+
+struct DoneMsg {
+  struct aes_server* s;
+  int slot;
+};
+
+// A host destination needs device staging; a device destination doubles as the staging.
+bool needs_staging(const aes_request& r) { return !r.dst_on_device; }
+
+}  // namespace
+
+struct aes_server {
+  aes_server_cfg cfg{};
+  aes_keypool* pool = nullptr;
+  int device = -1;
+  uint8_t* arena_base = nullptr;
+  Arena arena;
+  std::vector<StreamSlot> slots;
+  std::vector<DoneMsg> done_msgs;
+
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, Req> reqs;
+  std::vector<int> finished_slots;  // posted by stream callbacks
+  std::vector<double> finished_time;
+  uint64_t next_ticket = 1;
+  uint64_t inflight = 0;
+  bool stop = false;
+  std::thread worker;
+
+  // statistics
+  std::vector<double> lat_us;
+  uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, launched_reqs = 0, bytes_done = 0;
+  double t_first = 0, t_last = 0;
+};
+
+namespace {
+
+void CUDART_CB on_batch_done(void* p) {
+  DoneMsg* m = static_cast<DoneMsg*>(p);
+  aes_server* s = m->s;
+  const double t = now_s();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->finished_slots.push_back(m->slot);
+    s->finished_time.push_back(t);
+  }
+  s->cv_work.notify_one();
+}
+
+// Marks a slot's requests finished (state DONE or FAILED) and frees their staging.  Holds mu.
+void retire(aes_server* s, StreamSlot& sl, double t, int state) {
+  for (uint64_t tk : sl.tickets) {
+    auto it = s->reqs.find(tk);
+    if (it == s->reqs.end()) continue;
+    Req& q = it->second;
+    if (q.staged) s->arena.release(q.stage_off, q.stage_bytes);
+    q.staged = false;
+    q.state = state;
+    q.t_done = t;
+    --s->inflight;
+    if (state == AES_REQ_DONE) {
+      ++s->completed;
+      s->bytes_done += q.r.length;
+      s->lat_us.push_back((t - q.t_submit) * 1e6);
+      s->t_last = std::max(s->t_last, t);
+    } else {
+      ++s->failed;
+    }
+  }
+  sl.tickets.clear();
+  sl.busy = false;
+}
+
+// Issues the batch of `tickets` on slot i (mu NOT held; the requests are owned by this batch).
+aes_status issue(aes_server* s, int i, const std::vector<Req*>& batch) {
+  StreamSlot& sl = s->slots[i];
+  cudaStream_t st = sl.stream;
+  cudaError_t e;
+  if (s->cfg.fail_every && s->launches % s->cfg.fail_every == 0)  // launches n, 2n, 3n, ...: fake a failure
+    return set_error(AES_ECUDA, "injected launch failure (fail_every = %u)", s->cfg.fail_every);
+  std::vector<BatchMsg> enc, dec;
+  enc.reserve(batch.size());
+  dec.reserve(batch.size());
+  for (Req* q : batch) {
+    const aes_request& r = q->r;
+    uint64_t in_addr, out_addr;
+    if (r.src_on_device && r.dst_on_device) {
+      in_addr = reinterpret_cast<uint64_t>(r.src);
+      out_addr = reinterpret_cast<uint64_t>(r.dst);
+    } else if (!r.src_on_device && r.dst_on_device) {
+      if ((e = cudaMemcpyAsync(r.dst, r.src, r.length, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_error(e, "H2D");
+      in_addr = out_addr = reinterpret_cast<uint64_t>(r.dst);
+    } else {
+      uint8_t* stage = s->arena_base + q->stage_off;
+      if (r.src_on_device) in_addr = reinterpret_cast<uint64_t>(r.src);
+      else {
+        if ((e = cudaMemcpyAsync(stage, r.src, r.length, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_error(e, "H2D");
+        in_addr = reinterpret_cast<uint64_t>(stage);
+      }
+      out_addr = reinterpret_cast<uint64_t>(stage);
+    }
+    const BatchMsg d{r.key_idx, 0u, in_addr / 16, out_addr / 16, r.length / 16};
+    (r.dir == AES_ENCRYPT ? enc : dec).push_back(d);
+  }
+  auto fill = [&](BatchMsg* em, BatchMsg* dm) {
+    if (!enc.empty()) std::memcpy(em, enc.data(), enc.size() * sizeof(BatchMsg));
+    if (!dec.empty()) std::memcpy(dm, dec.data(), dec.size() * sizeof(BatchMsg));
+  };
+  aes_status rc = batch_launch_descs(sl.batch, enc.size(), dec.size(), fill, 0, 0, st);
+  if (rc != AES_OK) return rc;
+  for (Req* q : batch) {
+    const aes_request& r = q->r;
+    if (!r.dst_on_device)
+      if ((e = cudaMemcpyAsync(r.dst, s->arena_base + q->stage_off, r.length, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_error(e, "D2H");
+  }
+  if ((e = cudaLaunchHostFunc(st, on_batch_done, &s->done_msgs[i])) != cudaSuccess) return cuda_error(e, "cudaLaunchHostFunc");
+  return AES_OK;
+}
+
+void worker_main(aes_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    // 1. retire finished batches
+    for (size_t k = 0; k < s->finished_slots.size(); ++k)
+      retire(s, s->slots[s->finished_slots[k]], s->finished_time[k], AES_REQ_DONE);
+    if (!s->finished_slots.empty()) {
+      s->finished_slots.clear();
+      s->finished_time.clear();
+      s->cv_done.notify_all();
+    }
+    bool any_busy = false;
+    int free_slot = -1;
+    for (size_t i = 0; i < s->slots.size(); ++i) {
+      if (s->slots[i].busy) any_busy = true;
+      else if (free_slot < 0) free_slot = int(i);
+    }
+    if (s->stop) {
+      // fail whatever is still queued, then wait for the GPU to finish what it has
+      while (!s->queue.empty()) {
+        auto it = s->reqs.find(s->queue.front());
+        s->queue.pop_front();
+        if (it != s->reqs.end()) { it->second.state = AES_REQ_FAILED; ++s->failed; }
+      }
+      s->cv_done.notify_all();
+      if (!any_busy) break;
+      s->cv_work.wait(lk);
+      continue;
+    }
+    if (free_slot < 0 || s->queue.empty()) {
+      s->cv_work.wait(lk);
+      continue;
+    }
+    // 2. admit from the head of the queue into one batch
+    std::vector<Req*> batch;
+    std::vector<uint64_t> tickets;
+    while (!s->queue.empty() && batch.size() < s->cfg.max_batch && s->inflight < s->cfg.max_inflight) {
+      const uint64_t tk = s->queue.front();
+      auto it = s->reqs.find(tk);
+      if (it == s->reqs.end()) { s->queue.pop_front(); continue; }
+      Req& q = it->second;
+      if (needs_staging(q.r)) {
+        size_t off = 0;
+        if (!s->arena.alloc(q.r.length, &off)) break;  // wait for staging to free up
+        q.staged = true;
+        q.stage_off = off;
+        q.stage_bytes = q.r.length;
+      }
+      s->queue.pop_front();
+      ++s->inflight;
+      batch.push_back(&q);
+      tickets.push_back(tk);
+    }
+    if (batch.empty()) {
+      if (!any_busy) {
+        // nothing in flight and the head does not fit: it can never fit (checked at submit)
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+      } else {
+        s->cv_work.wait(lk);
+      }
+      continue;
+    }
+    StreamSlot& sl = s->slots[free_slot];
+    sl.busy = true;
+    sl.tickets = tickets;
+    ++s->launches;
+    s->launched_reqs += batch.size();
+    lk.unlock();
+    const aes_status rc = issue(s, free_slot, batch);
+    lk.lock();
+    if (rc != AES_OK) {
+      // nothing was enqueued after the failure point that could still touch the staging of
+      // this batch except copies already queued; wait for the stream before freeing it
+      lk.unlock();
+      cudaStreamSynchronize(sl.stream);
+      lk.lock();
+      retire(s, sl, now_s(), AES_REQ_FAILED);
+      s->cv_done.notify_all();
+    }
+  }
+}
+
+aes_status validate(const aes_server* s, const aes_request* r) {
+  if (!r) return set_error(AES_EINVAL, "null request");
+  if (r->dir != AES_ENCRYPT && r->dir != AES_DECRYPT) return set_error(AES_EINVAL, "bad dir %u", r->dir);
+  if (r->length == 0 || (r->length & 15u)) return set_error(AES_EINVAL, "length must be a positive multiple of 16");
+  if (!r->src || !r->dst) return set_error(AES_EINVAL, "null buffer");
+  if ((r->src_on_device && (reinterpret_cast<uintptr_t>(r->src) & 15u)) ||
+      (r->dst_on_device && (reinterpret_cast<uintptr_t>(r->dst) & 15u)))
+    return set_error(AES_EINVAL, "device buffers must be 16-byte aligned");
+  if (size_t(r->key_idx) >= s->pool->capacity || s->pool->nr[r->key_idx] == 0)
+    return set_error(AES_EINVAL, "key slot %u is not loaded", r->key_idx);
+  if (needs_staging(*r) && ((r->length + 255) & ~uint64_t(255)) > s->cfg.hbm_budget)
+    return set_error(AES_ENOMEM, "request of %llu bytes exceeds the staging budget of %llu bytes",
+                     (unsigned long long)r->length, (unsigned long long)s->cfg.hbm_budget);
+  return AES_OK;
+}
+
+}  // namespace
+
+using namespace aesgb;
+
+extern "C" {
+
+aes_status aes_server_destroy(aes_server* s) {
+  clear_error();
+  if (!s) return AES_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (StreamSlot& sl : s->slots) {
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.batch) aes_batch_destroy(sl.batch);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+  }
+  if (s->arena_base) cudaFree(s->arena_base);
+  delete s;
+  return AES_OK;
+}
+
+aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_server** out) {
+  clear_error();
+  if (!out) return set_error(AES_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!cfg || !pool || !pool->entries) return set_error(AES_EINVAL, "null config or key pool");
+  if (cfg->hbm_budget < (1u << 20) || cfg->max_inflight == 0 || cfg->nstreams == 0 || cfg->nstreams > 16 ||
+      cfg->max_batch == 0 || cfg->max_batch > 65536 || cfg->queue_capacity == 0)
+    return set_error(AES_EINVAL, "bad server configuration (budget >= 1 MiB, 1..16 streams, 1..65536 per batch)");
+  aes_server* s = new (std::nothrow) aes_server();
+  if (!s) return set_error(AES_ENOMEM, "host allocation failed");
+  s->cfg = *cfg;
+  s->pool = pool;
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e != cudaSuccess) { delete s; return cuda_error(e, "cudaGetDevice"); }
+  if (s->device != pool->device) { delete s; return set_error(AES_EINVAL, "pool is on another device"); }
+  size_t free_b = 0, total_b = 0;
+  if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) { delete s; return cuda_error(e, "cudaMemGetInfo"); }
+  if (cfg->hbm_budget > free_b) {
+    delete s;
+    return set_error(AES_ENOMEM, "staging budget %llu exceeds free device memory %zu", (unsigned long long)cfg->hbm_budget, free_b);
+  }
+  if ((e = cudaMalloc(&s->arena_base, cfg->hbm_budget)) != cudaSuccess) {
+    delete s;
+    return set_error(AES_ENOMEM, "staging arena cudaMalloc failed: %s", cudaGetErrorString(e));
+  }
+  s->arena.reset(cfg->hbm_budget);
+  s->slots.resize(cfg->nstreams);
+  s->done_msgs.resize(cfg->nstreams);
+  for (uint32_t i = 0; i < cfg->nstreams; ++i) {
+    s->done_msgs[i] = DoneMsg{s, int(i)};
+    if ((e = cudaStreamCreateWithFlags(&s->slots[i].stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      aes_server_destroy(s);
+      return cuda_error(e, "cudaStreamCreate");
+    }
+    aes_status st = aes_batch_create(pool, cfg->max_batch, &s->slots[i].batch);
+    if (st != AES_OK) {
+      aes_server_destroy(s);
+      return st;
+    }
+  }
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return AES_OK;
+}
+
+aes_status aes_server_submit(aes_server* s, const aes_request* req, uint64_t* ticket) {
+  clear_error();
+  if (!s || !ticket) return set_error(AES_EINVAL, "null server or ticket pointer");
+  aes_status st = validate(s, req);
+  if (st != AES_OK) return st;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return set_error(AES_EINVAL, "server is shutting down");
+    if (s->queue.size() >= s->cfg.queue_capacity) return set_error(AES_EAGAIN, "submission queue full (%u)", s->cfg.queue_capacity);
+    const uint64_t tk = s->next_ticket++;
+    Req q;
+    q.r = *req;
+    q.t_submit = now_s();
+    if (s->submitted == 0 || s->t_first == 0) s->t_first = q.t_submit;
+    ++s->submitted;
+    s->reqs.emplace(tk, q);
+    s->queue.push_back(tk);
+    *ticket = tk;
+  }
+  s->cv_work.notify_one();
+  return AES_OK;
+}
+
+aes_status aes_server_submit_many(aes_server* s, const aes_request* reqs, size_t n, uint64_t* tickets) {
+  clear_error();
+  if (!s || (n && (!reqs || !tickets))) return set_error(AES_EINVAL, "null server, request or ticket array");
+  for (size_t i = 0; i < n; ++i) {
+    aes_status st = validate(s, reqs + i);
+    if (st != AES_OK) {
+      char why[256];
+      std::snprintf(why, sizeof(why), "%s", aes_last_error());
+      return set_error(st, "request %zu: %s", i, why);
+    }
+  }
+  if (n == 0) return AES_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return set_error(AES_EINVAL, "server is shutting down");
+    if (s->queue.size() + n > s->cfg.queue_capacity)
+      return set_error(AES_EAGAIN, "submission queue has %zu free places, %zu requested",
+                       size_t(s->cfg.queue_capacity) - s->queue.size(), n);
+    const double t = now_s();
+    if (s->submitted == 0 || s->t_first == 0) s->t_first = t;
+    for (size_t i = 0; i < n; ++i) {
+      const uint64_t tk = s->next_ticket++;
+      Req q;
+      q.r = reqs[i];
+      q.t_submit = t;
+      s->reqs.emplace(tk, q);
+      s->queue.push_back(tk);
+      tickets[i] = tk;
+    }
+    s->submitted += n;
+  }
+  s->cv_work.notify_one();
+  return AES_OK;
+}
+
+aes_status aes_server_poll(aes_server* s, uint64_t ticket, int64_t timeout_us, int* state) {
+  clear_error();
+  if (!s || !state) return set_error(AES_EINVAL, "null server or state pointer");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return set_error(AES_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+  auto ready = [&] {
+    auto f = s->reqs.find(ticket);
+    return f == s->reqs.end() || f->second.state != AES_REQ_PENDING;
+  };
+  if (!ready() && timeout_us != 0) {
+    if (timeout_us < 0) s->cv_done.wait(lk, ready);
+    else s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+  }
+  it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return set_error(AES_ENOTFOUND, "ticket %llu was released by another poll", (unsigned long long)ticket);
+  const int stv = it->second.state;
+  *state = stv;
+  if (stv == AES_REQ_PENDING) return set_error(AES_ETIMEDOUT, "ticket %llu still pending", (unsigned long long)ticket);
+  s->reqs.erase(it);
+  return AES_OK;
+}
+
+aes_status aes_server_stats_get(aes_server* s, aes_server_stats* out) {
+  clear_error();
+  if (!s || !out) return set_error(AES_EINVAL, "null server or output");
+  std::vector<double> lat;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->failed = s->failed;
+    out->queued = s->queue.size();
+    out->inflight = s->inflight;
+    out->launches = s->launches;
+    out->bytes_completed = s->bytes_done;
+    out->mean_batch = s->launches ? double(s->launched_reqs) / double(s->launches) : 0.0;
+    out->gbps = (s->t_last > s->t_first && s->t_first > 0) ? s->bytes_done / (s->t_last - s->t_first) / 1e9 : 0.0;
+    lat = s->lat_us;
+  }
+  if (!lat.empty()) {
+    std::sort(lat.begin(), lat.end());
+    auto pct = [&](double p) {
+      const size_t k = size_t(std::min<double>(lat.size() - 1, std::max(0.0, std::ceil(p * lat.size()) - 1)));
+      return lat[k];
+    };
+    out->p50_us = pct(0.50);
+    out->p99_us = pct(0.99);
+    out->max_us = lat.back();
+    double sum = 0;
+    for (double v : lat) sum += v;
+    out->mean_us = sum / lat.size();
+  }
+  return AES_OK;
+}
+
+aes_status aes_server_stats_reset(aes_server* s) {
+  clear_error();
+  if (!s) return set_error(AES_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->lat_us.clear();
+  s->submitted = s->completed = s->failed = s->launches = s->launched_reqs = s->bytes_done = 0;
+  s->t_first = s->t_last = 0;
+  return AES_OK;
+}
+
+}  // extern "C"

@@ -74,47 +74,53 @@ __device__ __forceinline__ void fill_tables(uint32_t* sm) {
   }
 }
 
-template <int NR>
-__device__ __forceinline__ uint4 enc_block(uint4 v, const KeyWords& kw, const char* sm, uint32_t lc) {
-  uint32_t s0 = v.x ^ kw.w[0][0], s1 = v.y ^ kw.w[0][1], s2 = v.z ^ kw.w[0][2], s3 = v.w ^ kw.w[0][3];
-#pragma unroll
-  for (int r = 1; r < NR; ++r) {
-    // column c takes row i from column c + i (ShiftRows) through T_i
-    const uint32_t t0 = tt<0, 0>(sm, s0, lc) ^ tt<1, 1>(sm, s1, lc) ^ tt<2, 2>(sm, s2, lc) ^ tt<3, 3>(sm, s3, lc) ^ kw.w[r][0];
-    const uint32_t t1 = tt<0, 0>(sm, s1, lc) ^ tt<1, 1>(sm, s2, lc) ^ tt<2, 2>(sm, s3, lc) ^ tt<3, 3>(sm, s0, lc) ^ kw.w[r][1];
-    const uint32_t t2 = tt<0, 0>(sm, s2, lc) ^ tt<1, 1>(sm, s3, lc) ^ tt<2, 2>(sm, s0, lc) ^ tt<3, 3>(sm, s1, lc) ^ kw.w[r][2];
-    const uint32_t t3 = tt<0, 0>(sm, s3, lc) ^ tt<1, 1>(sm, s0, lc) ^ tt<2, 2>(sm, s1, lc) ^ tt<3, 3>(sm, s2, lc) ^ kw.w[r][3];
-    s0 = t0; s1 = t1; s2 = t2; s3 = t3;
+// One middle round on the four column words: encryption takes row i of column c + i through
+// T_i (ShiftRows + SubBytes + MixColumns), decryption row i of column c - i through Td_i.
+template <int DIR>
+__device__ __forceinline__ void tt_round(uint32_t& s0, uint32_t& s1, uint32_t& s2, uint32_t& s3, uint32_t k0,
+                                         uint32_t k1, uint32_t k2, uint32_t k3, const char* sm, uint32_t lc) {
+  uint32_t t0, t1, t2, t3;
+  if constexpr (DIR == AES_ENCRYPT) {
+    t0 = tt<0, 0>(sm, s0, lc) ^ tt<1, 1>(sm, s1, lc) ^ tt<2, 2>(sm, s2, lc) ^ tt<3, 3>(sm, s3, lc) ^ k0;
+    t1 = tt<0, 0>(sm, s1, lc) ^ tt<1, 1>(sm, s2, lc) ^ tt<2, 2>(sm, s3, lc) ^ tt<3, 3>(sm, s0, lc) ^ k1;
+    t2 = tt<0, 0>(sm, s2, lc) ^ tt<1, 1>(sm, s3, lc) ^ tt<2, 2>(sm, s0, lc) ^ tt<3, 3>(sm, s1, lc) ^ k2;
+    t3 = tt<0, 0>(sm, s3, lc) ^ tt<1, 1>(sm, s0, lc) ^ tt<2, 2>(sm, s1, lc) ^ tt<3, 3>(sm, s2, lc) ^ k3;
+  } else {
+    t0 = tt<0, 0>(sm, s0, lc) ^ tt<1, 1>(sm, s3, lc) ^ tt<2, 2>(sm, s2, lc) ^ tt<3, 3>(sm, s1, lc) ^ k0;
+    t1 = tt<0, 0>(sm, s1, lc) ^ tt<1, 1>(sm, s0, lc) ^ tt<2, 2>(sm, s3, lc) ^ tt<3, 3>(sm, s2, lc) ^ k1;
+    t2 = tt<0, 0>(sm, s2, lc) ^ tt<1, 1>(sm, s1, lc) ^ tt<2, 2>(sm, s0, lc) ^ tt<3, 3>(sm, s3, lc) ^ k2;
+    t3 = tt<0, 0>(sm, s3, lc) ^ tt<1, 1>(sm, s2, lc) ^ tt<2, 2>(sm, s1, lc) ^ tt<3, 3>(sm, s0, lc) ^ k3;
   }
-  // Last round: no MixColumns.  S(x) is byte 0 of T2 and T3, byte 1 of T3 and T0, byte 2 of
-  // T0 and T1, byte 3 of T1 and T2.
+  s0 = t0; s1 = t1; s2 = t2; s3 = t3;
+}
+
+// Last round (no MixColumns).  Encryption: S(x) is byte 0 of T2 and T3, byte 1 of T3 and T0,
+// byte 2 of T0 and T1, byte 3 of T1 and T2.  Decryption: region 2 holds InvS(x) in every byte.
+template <int DIR>
+__device__ __forceinline__ uint4 tt_final(uint32_t s0, uint32_t s1, uint32_t s2, uint32_t s3, uint32_t k0,
+                                          uint32_t k1, uint32_t k2, uint32_t k3, const char* sm, uint32_t lc) {
   uint4 o;
-  o.x = pick_bytes(tt<2, 0>(sm, s0, lc), tt<3, 1>(sm, s1, lc), tt<0, 2>(sm, s2, lc), tt<1, 3>(sm, s3, lc)) ^ kw.w[NR][0];
-  o.y = pick_bytes(tt<2, 0>(sm, s1, lc), tt<3, 1>(sm, s2, lc), tt<0, 2>(sm, s3, lc), tt<1, 3>(sm, s0, lc)) ^ kw.w[NR][1];
-  o.z = pick_bytes(tt<2, 0>(sm, s2, lc), tt<3, 1>(sm, s3, lc), tt<0, 2>(sm, s0, lc), tt<1, 3>(sm, s1, lc)) ^ kw.w[NR][2];
-  o.w = pick_bytes(tt<2, 0>(sm, s3, lc), tt<3, 1>(sm, s0, lc), tt<0, 2>(sm, s1, lc), tt<1, 3>(sm, s2, lc)) ^ kw.w[NR][3];
+  if constexpr (DIR == AES_ENCRYPT) {
+    o.x = pick_bytes(tt<2, 0>(sm, s0, lc), tt<3, 1>(sm, s1, lc), tt<0, 2>(sm, s2, lc), tt<1, 3>(sm, s3, lc)) ^ k0;
+    o.y = pick_bytes(tt<2, 0>(sm, s1, lc), tt<3, 1>(sm, s2, lc), tt<0, 2>(sm, s3, lc), tt<1, 3>(sm, s0, lc)) ^ k1;
+    o.z = pick_bytes(tt<2, 0>(sm, s2, lc), tt<3, 1>(sm, s3, lc), tt<0, 2>(sm, s0, lc), tt<1, 3>(sm, s1, lc)) ^ k2;
+    o.w = pick_bytes(tt<2, 0>(sm, s3, lc), tt<3, 1>(sm, s0, lc), tt<0, 2>(sm, s1, lc), tt<1, 3>(sm, s2, lc)) ^ k3;
+  } else {
+    o.x = pick_bytes(tt<4, 0>(sm, s0, lc), tt<4, 1>(sm, s3, lc), tt<4, 2>(sm, s2, lc), tt<4, 3>(sm, s1, lc)) ^ k0;
+    o.y = pick_bytes(tt<4, 0>(sm, s1, lc), tt<4, 1>(sm, s0, lc), tt<4, 2>(sm, s3, lc), tt<4, 3>(sm, s2, lc)) ^ k1;
+    o.z = pick_bytes(tt<4, 0>(sm, s2, lc), tt<4, 1>(sm, s1, lc), tt<4, 2>(sm, s0, lc), tt<4, 3>(sm, s3, lc)) ^ k2;
+    o.w = pick_bytes(tt<4, 0>(sm, s3, lc), tt<4, 1>(sm, s2, lc), tt<4, 2>(sm, s1, lc), tt<4, 3>(sm, s0, lc)) ^ k3;
+  }
   return o;
 }
 
-template <int NR>
-__device__ __forceinline__ uint4 dec_block(uint4 v, const KeyWords& kw, const char* sm, uint32_t lc) {
+// A whole block with NR rounds and the round keys in the constant bank (kernel parameter).
+template <int NR, int DIR>
+__device__ __forceinline__ uint4 crypt_block(uint4 v, const KeyWords& kw, const char* sm, uint32_t lc) {
   uint32_t s0 = v.x ^ kw.w[0][0], s1 = v.y ^ kw.w[0][1], s2 = v.z ^ kw.w[0][2], s3 = v.w ^ kw.w[0][3];
 #pragma unroll
-  for (int r = 1; r < NR; ++r) {
-    // InvShiftRows: column c takes row i from column c - i
-    const uint32_t t0 = tt<0, 0>(sm, s0, lc) ^ tt<1, 1>(sm, s3, lc) ^ tt<2, 2>(sm, s2, lc) ^ tt<3, 3>(sm, s1, lc) ^ kw.w[r][0];
-    const uint32_t t1 = tt<0, 0>(sm, s1, lc) ^ tt<1, 1>(sm, s0, lc) ^ tt<2, 2>(sm, s3, lc) ^ tt<3, 3>(sm, s2, lc) ^ kw.w[r][1];
-    const uint32_t t2 = tt<0, 0>(sm, s2, lc) ^ tt<1, 1>(sm, s1, lc) ^ tt<2, 2>(sm, s0, lc) ^ tt<3, 3>(sm, s3, lc) ^ kw.w[r][2];
-    const uint32_t t3 = tt<0, 0>(sm, s3, lc) ^ tt<1, 1>(sm, s2, lc) ^ tt<2, 2>(sm, s1, lc) ^ tt<3, 3>(sm, s0, lc) ^ kw.w[r][3];
-    s0 = t0; s1 = t1; s2 = t2; s3 = t3;
-  }
-  // Last round: InvS only (region 2 holds InvS(x) in every byte).
-  uint4 o;
-  o.x = pick_bytes(tt<4, 0>(sm, s0, lc), tt<4, 1>(sm, s3, lc), tt<4, 2>(sm, s2, lc), tt<4, 3>(sm, s1, lc)) ^ kw.w[NR][0];
-  o.y = pick_bytes(tt<4, 0>(sm, s1, lc), tt<4, 1>(sm, s0, lc), tt<4, 2>(sm, s3, lc), tt<4, 3>(sm, s2, lc)) ^ kw.w[NR][1];
-  o.z = pick_bytes(tt<4, 0>(sm, s2, lc), tt<4, 1>(sm, s1, lc), tt<4, 2>(sm, s0, lc), tt<4, 3>(sm, s3, lc)) ^ kw.w[NR][2];
-  o.w = pick_bytes(tt<4, 0>(sm, s3, lc), tt<4, 1>(sm, s2, lc), tt<4, 2>(sm, s1, lc), tt<4, 3>(sm, s0, lc)) ^ kw.w[NR][3];
-  return o;
+  for (int r = 1; r < NR; ++r) tt_round<DIR>(s0, s1, s2, s3, kw.w[r][0], kw.w[r][1], kw.w[r][2], kw.w[r][3], sm, lc);
+  return tt_final<DIR>(s0, s1, s2, s3, kw.w[NR][0], kw.w[NR][1], kw.w[NR][2], kw.w[NR][3], sm, lc);
 }
 
 __device__ __forceinline__ uint4 ld_block(const uint4* p) {
@@ -124,14 +130,13 @@ __device__ __forceinline__ uint4 ld_block(const uint4* p) {
   return v;
 }
 
-__device__ __forceinline__ void st_block(uint4* p, uint4 v) {
-  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+// Asks L2 to fetch the line holding p (no register result, no fault on any address).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
 }
 
-template <int NR, int DIR>
-__device__ __forceinline__ uint4 crypt_block(uint4 v, const KeyWords& kw, const char* sm, uint32_t lc) {
-  if constexpr (DIR == AES_ENCRYPT) return enc_block<NR>(v, kw, sm, lc);
-  else return dec_block<NR>(v, kw, sm, lc);
+__device__ __forceinline__ void st_block(uint4* p, uint4 v) {
+  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
 }
 
 template <int NR, int DIR, int THREADS, int U>
@@ -148,6 +153,9 @@ tt_kernel(const uint4* in, uint4* out, size_t nblocks, const KeyWords kw) {
     uint4 v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) v[u] = ld_block(in + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < U; ++u)  // the next iteration's blocks, while this one computes
+      if (i + (U + u) * stride < nblocks) prefetch_l2(in + i + (U + u) * stride);
 #pragma unroll
     for (int u = 0; u < U; ++u) v[u] = crypt_block<NR, DIR>(v[u], kw, sm, lc);
 #pragma unroll

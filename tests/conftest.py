@@ -40,3 +40,8 @@ def cuda(aes):
         pytest.fail("GPU test run without a visible CUDA device")
     torch.cuda.init()
     return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="session")
+def aes_lib_ready(aes, cuda):
+    return aes

@@ -87,3 +87,24 @@ def test_binding_raises_with_message(aes):
     with pytest.raises(aes.AesError) as ei:
         aes.aes_crypt_blocks(ks, None, (1 << 40) + 8, 1 << 41, 4, "encrypt")
     assert ei.value.status == aes.AES_EINVAL and "aligned" in str(ei.value)
+
+
+def test_pool_and_batch_null_handling_without_gpu(aes):
+    lib = aes.lib()
+    h = ctypes.c_void_p()
+    assert lib.aes_keypool_create(0, ctypes.byref(h)) == aes.AES_EINVAL
+    assert lib.aes_keypool_create(1 << 30, ctypes.byref(h)) == aes.AES_EINVAL
+    assert lib.aes_keypool_create(16, None) == aes.AES_EINVAL
+    assert lib.aes_keypool_destroy(None) == aes.AES_OK
+    assert lib.aes_keypool_rounds(None, 0) == 0
+    assert lib.aes_batch_create(None, 16, ctypes.byref(h)) == aes.AES_EINVAL
+    assert lib.aes_batch_destroy(None) == aes.AES_OK
+    assert lib.aes_batch_run(None, None, 0, None, None, 0, None) == aes.AES_EINVAL
+    assert lib.aes_batch_set_shape(None, 512, 4) == aes.AES_EINVAL
+    assert lib.aes_crypt_batched(None, None, 0, None, None, 0, None) == aes.AES_EINVAL
+    assert lib.aes_crypt_host(None, None, None, None, 4, 0, 0, None) == aes.AES_EINVAL
+
+
+def test_message_struct_layout(aes):
+    assert ctypes.sizeof(aes.aes_msg) == 24 == aes.msg_dtype().itemsize
+    assert ctypes.sizeof(aes.aes_key_schedule) == 4 + 15 * 16
