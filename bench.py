@@ -209,36 +209,47 @@ def read_profile_traffic() -> float | None:
 
 def measure_batched(aes, torch, dev, steps: int, plain_gbs: float) -> dict:
     """4096 messages, lognormal lengths (median 4 KiB, sigma 1.5), one AES-128 key each (seed 3),
-    encrypted in one autotuned persistent launch per step; L2 is flushed between steps."""
+    encrypted in one autotuned persistent launch per step.  Four copies of the 52.6 MB workload
+    sit at different places in device memory and the steps cycle through them back to back, so
+    every batch reads data that three batches (over 300 MB of traffic) have pushed out of L2;
+    the host prepares batch k+1 while the GPU runs batch k, as a pipelined caller would."""
     m = workloads.batched_messages(3)
     total = int(m.lengths.sum())
+    copies = 4
     msgs = np.zeros(len(m.lengths), dtype=aes.msg_dtype())
     msgs["key_idx"] = np.arange(len(m.lengths))
     msgs["offset"], msgs["length"] = m.offsets, m.lengths
     stream = torch.cuda.current_stream()
     with aes.KeyPool(len(m.keys)) as pool:
         pool.load_keys(0, m.keys, 128)
-        x = torch.from_numpy(m.data).to(dev)
+        x = torch.from_numpy(np.tile(m.data, copies)).to(dev)
         y = torch.empty_like(x)
-        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
         with aes.Batch(pool, len(m.lengths)) as b:
             shape = b.autotune(msgs, x.data_ptr(), y.data_ptr(), total)
-            for _ in range(3):
-                b.run(msgs, x.data_ptr(), y.data_ptr(), total)
-            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-            for k in range(steps):
-                flush.fill_(k & 0xFF)
-                evs[k][0].record(stream)
-                b.run(msgs, x.data_ptr(), y.data_ptr(), total)
-                evs[k][1].record(stream)
+            ptrs = [(x.data_ptr() + k * total, y.data_ptr() + k * total) for k in range(copies)]
+            for k in range(2 * copies):
+                b.run(msgs, *ptrs[k % copies], total)
             torch.cuda.synchronize()
-            ms = [a.elapsed_time(c) for a, c in evs]
-    gbs = total * len(ms) / (sum(ms) / 1e3) / 1e9
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(steps):
+                b.run(msgs, *ptrs[k % copies], total)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            # host cost of one run with the GPU idle
+            import time as _t
+            t = _t.perf_counter()
+            b.run(msgs, *ptrs[0], total)
+            host_us = (_t.perf_counter() - t) * 1e6
+            torch.cuda.synchronize()
+    gbs = total / (ms / 1e3) / 1e9
     return {"workload": "4096 msgs, lognormal(median 4 KiB, sigma 1.5) in [16 B, 16 MiB], own AES-128 key each, seed 3",
-            "bytes": total, "value": gbs, "unit": UNIT, "ms_per_batch": sum(ms) / len(ms),
+            "bytes": total, "value": gbs, "unit": UNIT, "ms_per_batch": ms, "host_us_per_run": host_us,
             "shape": {"threads": shape[0], "blocks_per_lane": shape[1]},
             "vs_plain_kernel": gbs / plain_gbs if plain_gbs else None,
-            "l2": "flushed (256 MiB write) before every timed batch", "launch": "aes_batch_run (CUDA graph replay)"}
+            "l2": "4 copies of the workload cycled (each batch's input last touched >300 MB of traffic ago)",
+            "launch": "aes_batch_run back to back (descriptor upload on a copy stream + CUDA graph replay)"}
 
 
 def measure_served(aes, torch, dev, nreq: int, plain_gbs: float) -> dict:
@@ -250,16 +261,16 @@ def measure_served(aes, torch, dev, nreq: int, plain_gbs: float) -> dict:
 
     out = {"workload": "Poisson arrivals, 50/50 enc/dec, lognormal(median 4 KiB, sigma 1.5) in [64 B, 64 MiB], "
                        "1024-key pool (half AES-128, half AES-256), device-resident payloads, seed 4",
-           "requests_per_rate": nreq, "rates": []}
+           "requests_per_rate": nreq, "closed_loop_requests": 20 * nreq, "rates": []}
     w0 = workloads.served_requests(4, 1, 1.0)
     pool = aes.KeyPool(len(w0.pool_keys))
     pool.load_keys(0, np.stack(w0.pool_keys[:512]), 128)
     pool.load_keys(512, np.stack(w0.pool_keys[512:]), 256)
     srv = aes.Server(pool, hbm_budget=1 << 30, max_inflight=1 << 20, nstreams=4, max_batch=8192,
-                     queue_capacity=1 << 22)
+                     queue_capacity=1 << 18)
     try:
         for rate in (1000.0, 10000.0, 100000.0, None):
-            w = workloads.served_requests(4, nreq if rate else 4 * nreq, rate or 1e9)
+            w = workloads.served_requests(4, nreq if rate else 20 * nreq, rate or 1e9)
             offs = np.concatenate([[0], np.cumsum(w.lengths)[:-1]]).astype(np.int64)
             total = int(w.lengths.sum())
             src = torch.randint(0, 256, (total,), dtype=torch.uint8, device=dev)

@@ -51,10 +51,16 @@ class aes_msg(ctypes.Structure):
                 ("length", ctypes.c_uint64)]
 
 
+_MSG_DTYPE = None
+
+
 # numpy view of an aes_msg array (same layout, 24 bytes)
 def msg_dtype():
-    import numpy as np
-    return np.dtype([("key_idx", "<u4"), ("dir", "<u4"), ("offset", "<u8"), ("length", "<u8")])
+    global _MSG_DTYPE
+    if _MSG_DTYPE is None:
+        import numpy as np
+        _MSG_DTYPE = np.dtype([("key_idx", "<u4"), ("dir", "<u4"), ("offset", "<u8"), ("length", "<u8")])
+    return _MSG_DTYPE
 
 
 class aes_server_cfg(ctypes.Structure):
@@ -225,8 +231,11 @@ def aes_crypt_host(ks: aes_key_schedule, iv, h_in: int, h_out: int, nblocks: int
 def _msgs_ptr(msgs):
     """msgs: numpy array of msg_dtype() (or a list of (key_idx, dir, offset, length))."""
     import numpy as np
-    a = np.ascontiguousarray(msgs if isinstance(msgs, np.ndarray) else np.array(msgs, dtype=msg_dtype()),
-                             dtype=msg_dtype())
+    dt = msg_dtype()
+    if isinstance(msgs, np.ndarray) and msgs.dtype == dt and msgs.flags["C_CONTIGUOUS"]:
+        a = msgs
+    else:
+        a = np.ascontiguousarray(msgs if isinstance(msgs, np.ndarray) else np.array(msgs, dtype=dt), dtype=dt)
     return a, a.ctypes.data, a.shape[0]
 
 
@@ -312,7 +321,7 @@ class Server:
     """Continuous-batching request server (aes_server_*)."""
 
     def __init__(self, pool: KeyPool, hbm_budget: int = 1 << 30, max_inflight: int = 1 << 16, nstreams: int = 4,
-                 max_batch: int = 4096, queue_capacity: int = 1 << 20, fail_every: int = 0):
+                 max_batch: int = 4096, queue_capacity: int = 1 << 16, fail_every: int = 0):
         cfg = aes_server_cfg(hbm_budget, max_inflight, nstreams, max_batch, queue_capacity, fail_every, 0)
         h = _VP()
         _check(lib().aes_server_create(ctypes.byref(cfg), pool.handle, ctypes.byref(h)))

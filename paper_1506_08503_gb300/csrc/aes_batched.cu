@@ -52,17 +52,39 @@ struct Slot {
 };
 
 struct Layout {
-  size_t enc_msgs, dec_msgs, enc_start, dec_start, end;
+  size_t enc_msgs, dec_msgs, enc_start, dec_start, enc_warp, dec_warp, end;
 };
 
-Layout layout(size_t nenc, size_t ndec) {
+// wmax: most warps a launch can have (SMs x 512 threads / 32)
+Layout layout(size_t nenc, size_t ndec, size_t wmax) {
   Layout l;
   l.enc_msgs = 0;
   l.dec_msgs = l.enc_msgs + nenc * sizeof(BatchMsg);
   l.enc_start = l.dec_msgs + ndec * sizeof(BatchMsg);
   l.dec_start = l.enc_start + (nenc + 1) * sizeof(uint64_t);
-  l.end = l.dec_start + (ndec + 1) * sizeof(uint64_t);
+  l.enc_warp = l.dec_start + (ndec + 1) * sizeof(uint64_t);
+  l.dec_warp = l.enc_warp + wmax * sizeof(uint32_t);
+  l.end = l.dec_warp + wmax * sizeof(uint32_t);
   return l;
+}
+
+// First message of every warp's slice: warp w of nw starts at block floor(total * w / nw).
+// The quotient is advanced incrementally (no division per warp).
+void warp_starts(const uint64_t* start, size_t nmsgs, uint64_t total, uint64_t nw, uint32_t* out) {
+  if (nw == 0) return;
+  const uint64_t step = total / nw, rem = total % nw;
+  uint64_t lo = 0, r = 0;
+  size_t m = 0;
+  for (uint64_t w = 0; w < nw; ++w) {
+    while (m + 1 < nmsgs && start[m + 1] <= lo) ++m;
+    out[w] = uint32_t(m);
+    lo += step;
+    r += rem;
+    if (r >= nw) {
+      ++lo;
+      r -= nw;
+    }
+  }
 }
 
 }  // namespace
@@ -72,6 +94,7 @@ struct aes_batch {
   int device = -1;
   size_t max_msgs = 0;
   size_t bytes = 0;
+  size_t wmax = 0;
   int threads = 512, bpl = 2;
   Slot slot[2];
   int next = 0;
@@ -132,7 +155,7 @@ aes_status build_graph(aes_batch* b, Slot& s, const cudaKernelNodeParams& pe, co
 }
 
 bool same_dir(const BatchDir& a, const BatchDir& b) {
-  return a.msgs == b.msgs && a.start == b.start && a.total == b.total && a.nmsgs == b.nmsgs;
+  return a.msgs == b.msgs && a.start == b.start && a.warp_msg == b.warp_msg && a.total == b.total && a.nmsgs == b.nmsgs;
 }
 
 // The kernels' dynamic shared-memory limit is raised once per device and kernel.
@@ -165,7 +188,7 @@ aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
   Slot& s = b->slot[b->next];
   b->next ^= 1;
   if ((e = cudaEventSynchronize(s.done)) != cudaSuccess) return cuda_error(e, "waiting for a previous batch");
-  const Layout L = layout(nenc, ndec);
+  const Layout L = layout(nenc, ndec, b->wmax);
   uint8_t* h = s.host;
   BatchMsg* em = reinterpret_cast<BatchMsg*>(h + L.enc_msgs);
   BatchMsg* dm = reinterpret_cast<BatchMsg*>(h + L.dec_msgs);
@@ -186,18 +209,22 @@ aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
   aes_status ast = ensure_smem_attr(fe, se);
   if (ast == AES_OK) ast = ensure_smem_attr(fd, sd);
   if (ast != AES_OK) return ast;
-  KernelArgs ae{in_base, out_base,
-                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.enc_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.enc_start),
-                         te, uint32_t(nenc), 0u},
-                b->pool->entries, {}};
-  KernelArgs ad{in_base, out_base,
-                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.dec_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.dec_start),
-                         td, uint32_t(ndec), 0u},
-                b->pool->entries, {}};
   // one CTA per SM (fewer when a direction has less than one block per thread)
   const uint64_t per_cta = uint64_t(b->threads);
   const unsigned ge = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(di->sms, (te + per_cta - 1) / per_cta)));
   const unsigned gd = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(di->sms, (td + per_cta - 1) / per_cta)));
+  const uint64_t nwe = uint64_t(ge) * (b->threads / 32), nwd = uint64_t(gd) * (b->threads / 32);
+  if (nwe > b->wmax || nwd > b->wmax) return set_error(AES_ECUDA, "device has more SMs than the batch was sized for");
+  warp_starts(es, nenc, te, nwe, reinterpret_cast<uint32_t*>(h + L.enc_warp));
+  warp_starts(ds, ndec, td, nwd, reinterpret_cast<uint32_t*>(h + L.dec_warp));
+  KernelArgs ae{in_base, out_base,
+                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.enc_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.enc_start),
+                         reinterpret_cast<const uint32_t*>(s.dev + L.enc_warp), te, uint32_t(nenc), 0u},
+                b->pool->entries, {}};
+  KernelArgs ad{in_base, out_base,
+                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.dec_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.dec_start),
+                         reinterpret_cast<const uint32_t*>(s.dev + L.dec_warp), td, uint32_t(ndec), 0u},
+                b->pool->entries, {}};
   const cudaKernelNodeParams pe = kernel_params(fe, ge, b->threads, se, ae);
   const cudaKernelNodeParams pd = kernel_params(fd, gd, b->threads, sd, ad);
   if (!s.exec || s.g_threads != b->threads || s.g_bpl != b->bpl) {
@@ -377,7 +404,10 @@ aes_status aes_batch_create(aes_keypool* pool, size_t max_msgs, aes_batch** out)
   cudaError_t e = cudaGetDevice(&b->device);
   if (e != cudaSuccess) { delete b; return cuda_error(e, "cudaGetDevice"); }
   if (b->device != pool->device) { delete b; return set_error(AES_EINVAL, "pool and batch on different devices"); }
-  b->bytes = layout(max_msgs, max_msgs).end;  // enough for any split of max_msgs
+  const DeviceInfo* di = current_device_info();
+  if (!di) { delete b; return AES_ECUDA; }
+  b->wmax = size_t(di->sms) * (512 / 32);
+  b->bytes = layout(max_msgs, max_msgs, b->wmax).end;  // enough for any split of max_msgs
   if ((e = cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) {
     delete b;
     return cuda_error(e, "cudaStreamCreate");

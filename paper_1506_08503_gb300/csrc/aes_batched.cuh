@@ -88,7 +88,10 @@ __device__ __forceinline__ uint4 crypt_rt(uint4 v, const uint32_t (&kw)[kMaxRoun
 // whole warp (uniform registers and branches), and each lane enciphers U independent blocks.
 // A window cut short by a message end leaves lanes idle; over lognormal lengths (median 4 KiB)
 // that costs a few percent, less than per-lane keys at the boundaries would.  The next window
-// of the same message is prefetched into L2 while the current one is enciphered.
+// of the same message is prefetched into L2 while the current one is enciphered.  The host
+// gives every warp the message holding its first block (warp_msg), so no warp searches.
+// (Measured alternatives that were slower: loading the next window into registers one window
+// ahead, and issuing the first window's loads before the table fill.)
 template <int DIR, int THREADS, int U>
 __global__ void __launch_bounds__(THREADS, 1)
 tt_batched_kernel(uint64_t in_base, uint64_t out_base, const BatchDir bd, const PoolEntry* pool) {
@@ -109,7 +112,7 @@ tt_batched_kernel(uint64_t in_base, uint64_t out_base, const BatchDir bd, const 
   uint32_t kl[4];
   int nr = 0;
   Cursor c;  // warp-uniform: the message holding block gb
-  open_msg(c, bd, find_msg(bd.start, bd.nmsgs, gb));
+  open_msg(c, bd, bd.warp_msg ? __ldg(bd.warp_msg + w) : find_msg(bd.start, bd.nmsgs, gb));
   load_key<DIR>(pool, c.key, kw, kl, nr);
   constexpr uint32_t kWin = 32u * U;
 

@@ -94,9 +94,12 @@ static_assert(sizeof(BatchMsg) == 32, "batch descriptors are 32 bytes");
 
 // Work of one direction: messages laid end to end; start[m] is the first block of message m
 // in that virtual block space (nmsgs + 1 entries, the last = total).
+// warp_msg[w] (optional, may be null) is the message holding warp w's first block when the
+// kernel runs with exactly nwarps = grid * threads / 32 warps.
 struct BatchDir {
   const BatchMsg* msgs;
   const uint64_t* start;
+  const uint32_t* warp_msg;
   uint64_t total;
   uint32_t nmsgs;
   uint32_t pad;

@@ -20,12 +20,10 @@
 #include <condition_variable>
 #include <cstdio>
 #include <cstring>
-#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "aes_internal.cuh"
@@ -82,9 +80,12 @@ class Arena {
   size_t size_ = 0;
 };
 
+// One request slot of the ring.  Ticket t lives in ring[t & mask] from submission until a
+// poll reports it finished; ticket == 0 marks a free slot.
 struct Req {
   aes_request r{};
-  double t_submit = 0, t_done = 0;
+  uint64_t ticket = 0;
+  double t_submit = 0;
   int state = AES_REQ_PENDING;
   bool staged = false;
   size_t stage_off = 0, stage_bytes = 0;
@@ -94,7 +95,8 @@ struct StreamSlot {
   cudaStream_t stream = nullptr;
   aes_batch* batch = nullptr;
   bool busy = false;
-  std::vector<uint64_t> tickets;
+  uint64_t first = 0, last = 0;    // the batch is the ticket range [first, last)
+  std::vector<BatchMsg> enc, dec;  // its descriptors (capacity reused)
 };
 
 struct DoneMsg {
@@ -118,11 +120,12 @@ struct aes_server {
 
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<uint64_t> queue;
-  std::unordered_map<uint64_t, Req> reqs;
+  std::vector<Req> ring;       // power-of-two size >= queue_capacity
+  uint64_t mask = 0;
+  uint64_t next_ticket = 1;    // next ticket to hand out
+  uint64_t admit = 1;          // first ticket not admitted yet: the queue is [admit, next_ticket)
   std::vector<int> finished_slots;  // posted by stream callbacks
   std::vector<double> finished_time;
-  uint64_t next_ticket = 1;
   uint64_t inflight = 0;
   bool stop = false;
   std::thread worker;
@@ -131,6 +134,8 @@ struct aes_server {
   std::vector<double> lat_us;
   uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, launched_reqs = 0, bytes_done = 0;
   double t_first = 0, t_last = 0;
+
+  Req& at(uint64_t t) { return ring[t & mask]; }
 };
 
 namespace {
@@ -149,40 +154,38 @@ void CUDART_CB on_batch_done(void* p) {
 
 // Marks a slot's requests finished (state DONE or FAILED) and frees their staging.  Holds mu.
 void retire(aes_server* s, StreamSlot& sl, double t, int state) {
-  for (uint64_t tk : sl.tickets) {
-    auto it = s->reqs.find(tk);
-    if (it == s->reqs.end()) continue;
-    Req& q = it->second;
+  for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
+    Req& q = s->at(tk);
     if (q.staged) s->arena.release(q.stage_off, q.stage_bytes);
     q.staged = false;
     q.state = state;
-    q.t_done = t;
     --s->inflight;
     if (state == AES_REQ_DONE) {
       ++s->completed;
       s->bytes_done += q.r.length;
       s->lat_us.push_back((t - q.t_submit) * 1e6);
-      s->t_last = std::max(s->t_last, t);
     } else {
       ++s->failed;
     }
   }
-  sl.tickets.clear();
+  if (state == AES_REQ_DONE && t > s->t_last) s->t_last = t;
   sl.busy = false;
 }
 
-// Issues the batch of `tickets` on slot i (mu NOT held; the requests are owned by this batch).
-aes_status issue(aes_server* s, int i, const std::vector<Req*>& batch) {
+// Issues the tickets [sl.first, sl.last) on slot i (mu NOT held; the batch owns its slots).
+aes_status issue(aes_server* s, int i) {
   StreamSlot& sl = s->slots[i];
   cudaStream_t st = sl.stream;
   cudaError_t e;
   if (s->cfg.fail_every && s->launches % s->cfg.fail_every == 0)  // launches n, 2n, 3n, ...: fake a failure
     return set_error(AES_ECUDA, "injected launch failure (fail_every = %u)", s->cfg.fail_every);
-  std::vector<BatchMsg> enc, dec;
-  enc.reserve(batch.size());
-  dec.reserve(batch.size());
-  for (Req* q : batch) {
-    const aes_request& r = q->r;
+  std::vector<BatchMsg>& enc = sl.enc;
+  std::vector<BatchMsg>& dec = sl.dec;
+  enc.clear();
+  dec.clear();
+  for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
+    const Req& q = s->at(tk);
+    const aes_request& r = q.r;
     uint64_t in_addr, out_addr;
     if (r.src_on_device && r.dst_on_device) {
       in_addr = reinterpret_cast<uint64_t>(r.src);
@@ -191,7 +194,7 @@ aes_status issue(aes_server* s, int i, const std::vector<Req*>& batch) {
       if ((e = cudaMemcpyAsync(r.dst, r.src, r.length, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_error(e, "H2D");
       in_addr = out_addr = reinterpret_cast<uint64_t>(r.dst);
     } else {
-      uint8_t* stage = s->arena_base + q->stage_off;
+      uint8_t* stage = s->arena_base + q.stage_off;
       if (r.src_on_device) in_addr = reinterpret_cast<uint64_t>(r.src);
       else {
         if ((e = cudaMemcpyAsync(stage, r.src, r.length, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_error(e, "H2D");
@@ -208,10 +211,10 @@ aes_status issue(aes_server* s, int i, const std::vector<Req*>& batch) {
   };
   aes_status rc = batch_launch_descs(sl.batch, enc.size(), dec.size(), fill, 0, 0, st);
   if (rc != AES_OK) return rc;
-  for (Req* q : batch) {
-    const aes_request& r = q->r;
-    if (!r.dst_on_device)
-      if ((e = cudaMemcpyAsync(r.dst, s->arena_base + q->stage_off, r.length, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+  for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
+    const Req& q = s->at(tk);
+    if (!q.r.dst_on_device)
+      if ((e = cudaMemcpyAsync(q.r.dst, s->arena_base + q.stage_off, q.r.length, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_error(e, "D2H");
   }
   if ((e = cudaLaunchHostFunc(st, on_batch_done, &s->done_msgs[i])) != cudaSuccess) return cuda_error(e, "cudaLaunchHostFunc");
@@ -238,28 +241,24 @@ void worker_main(aes_server* s) {
     }
     if (s->stop) {
       // fail whatever is still queued, then wait for the GPU to finish what it has
-      while (!s->queue.empty()) {
-        auto it = s->reqs.find(s->queue.front());
-        s->queue.pop_front();
-        if (it != s->reqs.end()) { it->second.state = AES_REQ_FAILED; ++s->failed; }
+      for (; s->admit < s->next_ticket; ++s->admit) {
+        s->at(s->admit).state = AES_REQ_FAILED;
+        ++s->failed;
       }
       s->cv_done.notify_all();
       if (!any_busy) break;
       s->cv_work.wait(lk);
       continue;
     }
-    if (free_slot < 0 || s->queue.empty()) {
+    if (free_slot < 0 || s->admit == s->next_ticket) {
       s->cv_work.wait(lk);
       continue;
     }
-    // 2. admit from the head of the queue into one batch
-    std::vector<Req*> batch;
-    std::vector<uint64_t> tickets;
-    while (!s->queue.empty() && batch.size() < s->cfg.max_batch && s->inflight < s->cfg.max_inflight) {
-      const uint64_t tk = s->queue.front();
-      auto it = s->reqs.find(tk);
-      if (it == s->reqs.end()) { s->queue.pop_front(); continue; }
-      Req& q = it->second;
+    // 2. admit from the head of the queue into one batch: the ticket range [admit, t)
+    const uint64_t first = s->admit;
+    uint64_t t = first;
+    while (t < s->next_ticket && t - first < s->cfg.max_batch && s->inflight < s->cfg.max_inflight) {
+      Req& q = s->at(t);
       if (needs_staging(q.r)) {
         size_t off = 0;
         if (!s->arena.alloc(q.r.length, &off)) break;  // wait for staging to free up
@@ -267,31 +266,26 @@ void worker_main(aes_server* s) {
         q.stage_off = off;
         q.stage_bytes = q.r.length;
       }
-      s->queue.pop_front();
       ++s->inflight;
-      batch.push_back(&q);
-      tickets.push_back(tk);
+      ++t;
     }
-    if (batch.empty()) {
-      if (!any_busy) {
-        // nothing in flight and the head does not fit: it can never fit (checked at submit)
-        s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
-      } else {
-        s->cv_work.wait(lk);
-      }
+    if (t == first) {
+      if (!any_busy) s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+      else s->cv_work.wait(lk);
       continue;
     }
+    s->admit = t;
     StreamSlot& sl = s->slots[free_slot];
     sl.busy = true;
-    sl.tickets = tickets;
+    sl.first = first;
+    sl.last = t;
     ++s->launches;
-    s->launched_reqs += batch.size();
+    s->launched_reqs += t - first;
     lk.unlock();
-    const aes_status rc = issue(s, free_slot, batch);
+    const aes_status rc = issue(s, free_slot);
     lk.lock();
     if (rc != AES_OK) {
-      // nothing was enqueued after the failure point that could still touch the staging of
-      // this batch except copies already queued; wait for the stream before freeing it
+      // copies queued before the failure may still read the staging: drain the stream first
       lk.unlock();
       cudaStreamSynchronize(sl.stream);
       lk.lock();
@@ -314,6 +308,34 @@ aes_status validate(const aes_server* s, const aes_request* r) {
   if (needs_staging(*r) && ((r->length + 255) & ~uint64_t(255)) > s->cfg.hbm_budget)
     return set_error(AES_ENOMEM, "request of %llu bytes exceeds the staging budget of %llu bytes",
                      (unsigned long long)r->length, (unsigned long long)s->cfg.hbm_budget);
+  return AES_OK;
+}
+
+// Places n requests (already validated) into the ring; caller holds mu and has checked room.
+void enqueue(aes_server* s, const aes_request* reqs, size_t n, uint64_t* tickets) {
+  const double t = now_s();
+  if (s->submitted == 0 || s->t_first == 0) s->t_first = t;
+  for (size_t i = 0; i < n; ++i) {
+    const uint64_t tk = s->next_ticket++;
+    Req& q = s->at(tk);
+    q.r = reqs[i];
+    q.ticket = tk;
+    q.t_submit = t;
+    q.state = AES_REQ_PENDING;
+    q.staged = false;
+    tickets[i] = tk;
+  }
+  s->submitted += n;
+}
+
+// Room for n more tickets: the queue limit, and the ring slots they land on must be free
+// (every earlier ticket that maps there has been released by a poll).
+aes_status room_for(const aes_server* s, size_t n) {
+  if (s->next_ticket - s->admit + n > s->cfg.queue_capacity)
+    return set_error(AES_EAGAIN, "submission queue full (%u)", s->cfg.queue_capacity);
+  for (size_t i = 0; i < n; ++i)
+    if (s->ring[(s->next_ticket + i) & s->mask].ticket != 0)
+      return set_error(AES_EAGAIN, "no free request slot: poll finished tickets to release them");
   return AES_OK;
 }
 
@@ -368,6 +390,16 @@ aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_s
     return set_error(AES_ENOMEM, "staging arena cudaMalloc failed: %s", cudaGetErrorString(e));
   }
   s->arena.reset(cfg->hbm_budget);
+  size_t ring = 1;
+  while (ring < cfg->queue_capacity) ring <<= 1;
+  try {
+    s->ring.resize(ring);
+    s->lat_us.reserve(std::min<size_t>(ring, size_t(1) << 22));
+  } catch (...) {
+    aes_server_destroy(s);
+    return set_error(AES_ENOMEM, "request ring of %zu entries could not be allocated", ring);
+  }
+  s->mask = ring - 1;
   s->slots.resize(cfg->nstreams);
   s->done_msgs.resize(cfg->nstreams);
   for (uint32_t i = 0; i < cfg->nstreams; ++i) {
@@ -395,16 +427,8 @@ aes_status aes_server_submit(aes_server* s, const aes_request* req, uint64_t* ti
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return set_error(AES_EINVAL, "server is shutting down");
-    if (s->queue.size() >= s->cfg.queue_capacity) return set_error(AES_EAGAIN, "submission queue full (%u)", s->cfg.queue_capacity);
-    const uint64_t tk = s->next_ticket++;
-    Req q;
-    q.r = *req;
-    q.t_submit = now_s();
-    if (s->submitted == 0 || s->t_first == 0) s->t_first = q.t_submit;
-    ++s->submitted;
-    s->reqs.emplace(tk, q);
-    s->queue.push_back(tk);
-    *ticket = tk;
+    if ((st = room_for(s, 1)) != AES_OK) return st;
+    enqueue(s, req, 1, ticket);
   }
   s->cv_work.notify_one();
   return AES_OK;
@@ -425,21 +449,9 @@ aes_status aes_server_submit_many(aes_server* s, const aes_request* reqs, size_t
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return set_error(AES_EINVAL, "server is shutting down");
-    if (s->queue.size() + n > s->cfg.queue_capacity)
-      return set_error(AES_EAGAIN, "submission queue has %zu free places, %zu requested",
-                       size_t(s->cfg.queue_capacity) - s->queue.size(), n);
-    const double t = now_s();
-    if (s->submitted == 0 || s->t_first == 0) s->t_first = t;
-    for (size_t i = 0; i < n; ++i) {
-      const uint64_t tk = s->next_ticket++;
-      Req q;
-      q.r = reqs[i];
-      q.t_submit = t;
-      s->reqs.emplace(tk, q);
-      s->queue.push_back(tk);
-      tickets[i] = tk;
-    }
-    s->submitted += n;
+    aes_status st = room_for(s, n);
+    if (st != AES_OK) return st;
+    enqueue(s, reqs, n, tickets);
   }
   s->cv_work.notify_one();
   return AES_OK;
@@ -449,22 +461,18 @@ aes_status aes_server_poll(aes_server* s, uint64_t ticket, int64_t timeout_us, i
   clear_error();
   if (!s || !state) return set_error(AES_EINVAL, "null server or state pointer");
   std::unique_lock<std::mutex> lk(s->mu);
-  auto it = s->reqs.find(ticket);
-  if (it == s->reqs.end()) return set_error(AES_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
-  auto ready = [&] {
-    auto f = s->reqs.find(ticket);
-    return f == s->reqs.end() || f->second.state != AES_REQ_PENDING;
-  };
+  auto known = [&] { return ticket != 0 && s->at(ticket).ticket == ticket; };
+  if (!known()) return set_error(AES_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+  auto ready = [&] { return !known() || s->at(ticket).state != AES_REQ_PENDING; };
   if (!ready() && timeout_us != 0) {
     if (timeout_us < 0) s->cv_done.wait(lk, ready);
     else s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
   }
-  it = s->reqs.find(ticket);
-  if (it == s->reqs.end()) return set_error(AES_ENOTFOUND, "ticket %llu was released by another poll", (unsigned long long)ticket);
-  const int stv = it->second.state;
-  *state = stv;
-  if (stv == AES_REQ_PENDING) return set_error(AES_ETIMEDOUT, "ticket %llu still pending", (unsigned long long)ticket);
-  s->reqs.erase(it);
+  if (!known()) return set_error(AES_ENOTFOUND, "ticket %llu was released by another poll", (unsigned long long)ticket);
+  Req& q = s->at(ticket);
+  *state = q.state;
+  if (q.state == AES_REQ_PENDING) return set_error(AES_ETIMEDOUT, "ticket %llu still pending", (unsigned long long)ticket);
+  q.ticket = 0;  // released: the slot can take a new request
   return AES_OK;
 }
 
@@ -478,7 +486,7 @@ aes_status aes_server_stats_get(aes_server* s, aes_server_stats* out) {
     out->submitted = s->submitted;
     out->completed = s->completed;
     out->failed = s->failed;
-    out->queued = s->queue.size();
+    out->queued = s->next_ticket - s->admit;
     out->inflight = s->inflight;
     out->launches = s->launches;
     out->bytes_completed = s->bytes_done;

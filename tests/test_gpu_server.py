@@ -93,18 +93,21 @@ def test_backpressure_and_bounded_waits(aes_lib_ready):
     with pool, aes.Server(pool, hbm_budget=8 << 20, nstreams=1, max_batch=2, queue_capacity=3) as srv:
         bufs = [(rng.integers(0, 256, 16 * 20000, dtype=np.uint8), np.empty(16 * 20000, dtype=np.uint8))
                 for _ in range(40)]
-        tickets, rejected = [], 0
-        while len(tickets) < 40:
-            a, b = bufs[len(tickets)]
+        outstanding, done, rejected, nsub = [], 0, 0, 0
+        while nsub < 40:
+            a, b = bufs[nsub]
             t = srv.try_submit(0, 0, a.ctypes.data, b.ctypes.data, a.size, False, False)
-            if t is None:
+            if t is None:  # AES_EAGAIN: release the oldest ticket, then retry
                 rejected += 1
-                time.sleep(0.0002)
+                assert srv.poll(outstanding.pop(0)) == aes.AES_REQ_DONE
+                done += 1
                 continue
-            tickets.append(t)
-        assert rejected > 0  # the queue filled up and said AES_EAGAIN
-        for t in tickets:
+            outstanding.append(t)
+            nsub += 1
+        assert rejected > 0  # the holding limit was reached and submit said AES_EAGAIN
+        for t in outstanding:
             assert srv.poll(t) == aes.AES_REQ_DONE
+        assert done + len(outstanding) == 40
         # bounded wait on a request that cannot be finished in 0 us
         big = rng.integers(0, 256, 8 << 20, dtype=np.uint8)
         out = np.empty_like(big)
