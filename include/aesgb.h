@@ -194,7 +194,9 @@ typedef struct {
   uint32_t max_inflight;    /* requests admitted but not completed (>= 1) */
   uint32_t nstreams;        /* concurrent batches, 1..16 */
   uint32_t max_batch;       /* requests per launch, 1..65536 */
-  uint32_t queue_capacity;  /* submitted but not admitted requests before AES_EAGAIN (>= 1) */
+  uint32_t queue_capacity;  /* requests held at once, from submission until a poll reports them
+                               finished (queued + running + finished-but-unpolled); beyond it
+                               submit returns AES_EAGAIN (>= 1; rounded up to a power of two) */
   uint32_t fail_every;      /* fault injection for tests: every n-th launch fails on the host
                                without touching the GPU (its requests end FAILED); 0 = off */
   uint32_t reserved;
@@ -227,8 +229,9 @@ typedef struct {
 aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_server** out);
 
 /* Queues a copy of *req and returns its ticket.  The caller keeps src/dst alive and untouched
- * until the ticket is reported done.  AES_EAGAIN if the queue is full, AES_EINVAL for a bad
- * request, AES_ENOMEM if it needs more staging than the whole budget. */
+ * until the ticket is reported done.  AES_EAGAIN if queue_capacity requests are already held
+ * (poll finished tickets to release them), AES_EINVAL for a bad request, AES_ENOMEM if it
+ * needs more staging than the whole budget. */
 aes_status aes_server_submit(aes_server* s, const aes_request* req, uint64_t* ticket);
 
 /* Queues n requests at once (host array), all or none: AES_EAGAIN if fewer than n queue
