@@ -180,6 +180,25 @@ aes_status aes_batch_destroy(aes_batch* b);
 aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsgs, const void* d_in,
                              void* d_out, size_t buf_bytes, void* cuda_stream);
 
+/* Batched encryption/decryption for callers that may not allocate device memory: for
+ * example a plug-in whose host application owns all device memory and only lends it input
+ * and output buffers, or a latency-critical path that cannot afford cudaMalloc's implicit
+ * device-wide synchronisation.  The paper has no counterpart to this entry point.
+ *
+ * Same cipher and message rules as aes_batch_run, except that the caller passes the expanded
+ * schedules directly (host array of nkeys <= 256 entries; msgs[i].key_idx indexes it) and at
+ * most 4096 messages; larger counts are AES_EINVAL.  Nothing is allocated: all working data
+ * lives in one static 320 KiB array in device memory that the library declares (present on
+ * every device that loads the library, until the process exits).  The first call on a device
+ * looks up that array's device address; make that first call before any stream capture.  The
+ * call copies its descriptors from pageable host memory, so it returns only after the work
+ * already queued on cuda_stream has finished.  All calls share the array: calls on one stream
+ * are ordered and safe, calls that overlap on the GPU (other streams, no synchronisation)
+ * race on it and may produce wrong output. */
+aes_status aes_crypt_batched_noalloc(const aes_key_schedule* schedules, uint32_t nkeys, const aes_msg* msgs,
+                                     size_t nmsgs, const void* d_in, void* d_out, size_t buf_bytes,
+                                     void* cuda_stream);
+
 /* ---------------------------------------------------------------------------------------
  * Request server with continuous batching.  A host thread owned by the server admits queued
  * requests while device staging memory (the HBM budget) and in-flight slots are free, packs
