@@ -80,6 +80,7 @@ def parse_args():
     p.add_argument("--no-batched", action="store_true", help="skip the 4096-message batched measurement")
     p.add_argument("--no-served", action="store_true", help="skip the served (request server) measurement")
     p.add_argument("--served-requests", type=int, default=10000, help="requests per offered rate")
+    p.add_argument("--no-cbc", action="store_true", help="skip the multi-block CBC measurement")
     return p.parse_args()
 
 
@@ -252,6 +253,38 @@ def measure_batched(aes, torch, dev, steps: int, plain_gbs: float) -> dict:
             "launch": "aes_batch_run back to back (descriptor upload on a copy stream + CUDA graph replay)"}
 
 
+def measure_cbc(aes, torch, dev) -> dict:
+    """The paper's CBC mode over whole messages (App. A1/A4): 128 messages of growing length
+    (the paper's second workload shape) and 2^18 messages of 16 blocks; AES-128, one IV per
+    message.  Encryption chains inside each message (one lane per message); decryption is
+    block-parallel.  GB/s of message bytes, CUDA events, 5 repetitions after 2 warm-ups."""
+    ks = aes.aes_key_expand(bytes(range(16)))
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n, m in ((128, 16), (128, 256), (128, 4096), (1 << 18, 16)):
+        x = torch.randint(0, 256, (n, 16 * m), dtype=torch.uint8, device=dev)
+        ivs = torch.randint(0, 256, (n, 16), dtype=torch.uint8, device=dev)
+        y = torch.empty_like(x)
+        z = torch.empty_like(x)
+        entry = {"messages": n, "blocks_per_message": m, "bytes": n * m * 16}
+        for d, src, dst in (("encrypt", x, y), ("decrypt", y, z)):
+            for _ in range(2):
+                aes.cbc(src, ks, ivs, d, out=dst)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                aes.cbc(src, ks, ivs, d, out=dst)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 5
+            entry[d + "_gbs"] = n * m * 16 / (ms / 1e3) / 1e9
+        torch.cuda.synchronize()
+        if not torch.equal(z, x):
+            raise RuntimeError("CBC round trip failed")
+        rows.append(entry)
+    return {"mode": "CBC over whole messages, AES-128, one IV per message", "rows": rows}
+
+
 def measure_served(aes, torch, dev, nreq: int, plain_gbs: float) -> dict:
     """The request server under Poisson arrivals (seed 4): 50/50 encrypt/decrypt, sizes
     lognormal (median 4 KiB, sigma 1.5) in [64 B, 64 MiB], keys from a resident pool of 1024
@@ -303,7 +336,13 @@ def measure_served(aes, torch, dev, nreq: int, plain_gbs: float) -> dict:
                      "mean_batch": st["mean_batch"], "launches": st["launches"],
                      "failed": int(sum(1 for x in states if x != aes.AES_REQ_DONE)), "bytes": total}
             if rate is None:
+                # the mix carries 14-round AES-256 requests: compare also against the plain
+                # kernel's rate scaled to the byte-weighted mean round count of this workload
+                rounds = np.where(w.key_idx < 512, 10.0, 14.0)
+                mean_rounds = float((rounds * w.lengths).sum() / w.lengths.sum())
                 entry["vs_plain_kernel"] = st["gbps"] / plain_gbs if plain_gbs else None
+                entry["mean_rounds_by_bytes"] = mean_rounds
+                entry["vs_plain_kernel_same_rounds"] = st["gbps"] / (plain_gbs * 10.0 / mean_rounds) if plain_gbs else None
                 out["closed_loop"] = entry
             else:
                 out["rates"].append(entry)
@@ -446,6 +485,10 @@ def run_ours(args):
     if not args.no_batched and rank == 0:
         batched = measure_batched(aes, torch, dev, max(10, min(args.steps, 50)), roofline["enc_gbs"])
 
+    cbc = None
+    if not args.no_cbc and rank == 0:
+        cbc = measure_cbc(aes, torch, dev)
+
     served = None
     if not args.no_served and rank == 0:
         served = measure_served(aes, torch, dev, args.served_requests, roofline["enc_gbs"])
@@ -476,7 +519,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "nblocks_per_rank": n, "key_bits": 128, "mode": "ECB (IV = 0)",
                        "kernel": args.kernel, "l2": "inputs (1 GiB) larger than L2 (129 MB); no flush"},
             "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk, "roofline": roofline,
-            "cpu_baseline": cpu, "batched": batched, "served": served,
+            "cpu_baseline": cpu, "batched": batched, "served": served, "cbc": cbc,
         }
         print(json.dumps(line))
     if dist is not None:

@@ -92,6 +92,18 @@ aes_status aes_decrypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, con
 aes_status aes_crypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, const void* d_in,
                             void* d_out, size_t nblocks, int dir, int impl, void* cuda_stream);
 
+/* The paper's CBC mode over whole messages (Section II; App. A1 encryption, App. A4
+ * decryption).  d_in and d_out (device) hold an nmsgs x (16 * blocks_per_msg) byte matrix, one
+ * message per row, rows back to back; row i is chained: C_j = E(P_j xor C_{j-1}) with
+ * C_{-1} = IV_i, and P_j = D(C_j) xor C_{j-1}.  d_ivs (device, 16-byte aligned) holds one
+ * 16-byte IV for every row (iv_per_msg = 0, the appendix's repeated IV) or one per row
+ * (iv_per_msg = 1, the IV matrix V of Section II).  Encryption runs one lane per message (the
+ * chain is serial inside a message), decryption one lane per block.  Encryption may run in
+ * place; decryption may not (each block needs the previous ciphertext): AES_EINVAL.  An empty
+ * matrix returns AES_OK. */
+aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_ivs, int iv_per_msg, const void* d_in,
+                         void* d_out, size_t nmsgs, size_t blocks_per_msg, int dir, void* cuda_stream);
+
 /* Same cipher on HOST buffers: the library copies the data to the device in 64 MiB chunks,
  * runs the kernel and copies the result back, overlapping the three on its own streams.
  *   h_in, h_out  host pointers (pinned memory gives full copy bandwidth; pageable works,

@@ -106,6 +106,8 @@ _SIGS: dict[str, tuple] = {
     "aes_decrypt_blocks": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _VP]),
     "aes_crypt_blocks": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _I, _I, _VP]),
     "aes_crypt_host": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _I, _I, _VP]),
+    "aes_cbc_crypt": (_I, [_KSP, _VP, _I, _VP, _VP, _SZ, _SZ, _I, _VP]),
+    "aes_crypt_batched_noalloc": (_I, [_KSP, ctypes.c_uint32, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "aes_keypool_create": (_I, [_SZ, ctypes.POINTER(_VP)]),
     "aes_keypool_load_keys": (_I, [_VP, ctypes.c_uint32, _SZ, _U8P, _I, _VP]),
     "aes_keypool_set": (_I, [_VP, ctypes.c_uint32, _KSP]),
@@ -224,6 +226,37 @@ def aes_crypt_host(ks: aes_key_schedule, iv, h_in: int, h_out: int, nblocks: int
     _check(lib().aes_crypt_host(ctypes.byref(ks), ivp[0] if ivp else None, h_in, h_out, nblocks,
                                 _dir(dir), _IMPLS[impl] if isinstance(impl, str) else int(impl),
                                 _stream_ptr(stream)))
+
+
+def aes_cbc_crypt(ks: aes_key_schedule, d_ivs: int, iv_per_msg: bool, d_in: int, d_out: int, nmsgs: int,
+                  blocks_per_msg: int, dir, stream=None) -> None:
+    """CBC over an nmsgs x blocks_per_msg matrix of blocks (device pointers)."""
+    _check(lib().aes_cbc_crypt(ctypes.byref(ks), d_ivs, int(iv_per_msg), d_in, d_out, nmsgs, blocks_per_msg,
+                               _dir(dir), _stream_ptr(stream)))
+
+
+def cbc(x, ks: aes_key_schedule, ivs, dir="encrypt", out=None, stream=None):
+    """CBC on a CUDA uint8 tensor of shape (nmsgs, 16 * blocks_per_msg); ivs is a CUDA uint8
+    tensor of 16 bytes (one IV for all rows) or (nmsgs, 16) (one per row)."""
+    import torch
+
+    if x.dim() != 2 or x.shape[1] % 16 or x.dtype != torch.uint8 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous (nmsgs, 16*m) uint8 tensor")
+    per_msg = ivs.numel() != 16
+    if per_msg and tuple(ivs.shape) != (x.shape[0], 16):
+        raise ValueError("ivs must hold 16 bytes or one 16-byte IV per row")
+    if out is None:
+        out = torch.empty_like(x)
+    aes_cbc_crypt(ks, ivs.data_ptr(), per_msg, x.data_ptr(), out.data_ptr(), x.shape[0], x.shape[1] // 16, dir,
+                  stream)
+    return out
+
+
+def aes_crypt_batched_noalloc(schedules, msgs, d_in: int, d_out: int, buf_bytes: int, stream=None) -> None:
+    """Allocation-free batched call: `schedules` is a ctypes array of aes_key_schedule."""
+    a, p, n = _msgs_ptr(msgs)
+    _check(lib().aes_crypt_batched_noalloc(schedules, len(schedules), p, n, d_in, d_out, buf_bytes,
+                                           _stream_ptr(stream)))
 
 
 # ---- key pool and batches -------------------------------------------------------------------

@@ -90,8 +90,9 @@ __device__ __forceinline__ uint4 crypt_rt(uint4 v, const uint32_t (&kw)[kMaxRoun
 // that costs a few percent, less than per-lane keys at the boundaries would.  The next window
 // of the same message is prefetched into L2 while the current one is enciphered.  The host
 // gives every warp the message holding its first block (warp_msg), so no warp searches.
-// (Measured alternatives that were slower: loading the next window into registers one window
-// ahead, and issuing the first window's loads before the table fill.)
+// (Measured alternatives that were slower: the next window loaded into registers one window
+// ahead; the first window issued before the table fill; a separate loop for whole windows,
+// whose second copy of the unrolled rounds costs more in instruction fetch than it saves.)
 template <int DIR, int THREADS, int U>
 __global__ void __launch_bounds__(THREADS, 1)
 tt_batched_kernel(uint64_t in_base, uint64_t out_base, const BatchDir bd, const PoolEntry* pool) {

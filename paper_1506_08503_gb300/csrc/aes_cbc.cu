@@ -1,0 +1,130 @@
+// aes_cbc.cu -- the paper's CBC mode over whole messages (Section II; App. A1 encryption,
+// App. A4 decryption): an N x M byte matrix of N messages with M bytes each, one IV per message
+// (or one IV for all, as the appendix does with a repeated IV), C_j = E(P_j ^ C_{j-1}) with
+// C_{-1} = IV, and P_j = D(C_j) ^ C_{j-1}.
+//
+// Encryption is a chain inside each message, so it runs one lane per message: the lane walks
+// its row block by block, keeping the chaining value in registers and loading the next block
+// while the current one is enciphered.  Neighbouring lanes hold neighbouring rows, so a warp
+// load touches 32 rows; the rows' next blocks sit in the same cache lines, which L1 keeps.
+// With enough messages (about 78K, one per lane of a full GPU) the shared-memory lookup rate
+// is the bound, as for independent blocks; with few messages the chain's latency is.
+//
+// Decryption has no chain: every block needs only its own ciphertext and the previous one, so
+// it runs one block per lane over the whole matrix like the independent-block kernel, with
+// one extra (mostly L1-hit) load of the previous block.  It cannot run in place.
+#include "aes_ttable.cuh"
+
+namespace aesgb {
+namespace {
+
+using namespace tt;
+
+__device__ __forceinline__ uint4 ld_cached(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) {
+  return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
+}
+
+// IVs: iv_stride 0 = one IV (16 bytes at ivs) for every message, 1 = one IV per message.
+template <int NR>
+__global__ void __launch_bounds__(512, 1)
+cbc_encrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride, uint64_t nmsgs, uint64_t mblocks,
+                   const KeyWords kw) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  fill_tables<AES_ENCRYPT>(smem);
+  __syncthreads();
+  const char* sm = reinterpret_cast<const char*>(smem);
+  const uint32_t lc = (threadIdx.x & 31u) * 4u;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t msg = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; msg < nmsgs; msg += stride) {
+    const uint4* src = in + msg * mblocks;
+    uint4* dst = out + msg * mblocks;
+    uint4 chain = ld_cached(ivs + (iv_stride ? msg : 0));
+    uint4 next = mblocks ? ld_cached(src) : make_uint4(0u, 0u, 0u, 0u);
+    for (uint64_t j = 0; j < mblocks; ++j) {
+      const uint4 p = next;
+      if (j + 1 < mblocks) next = ld_cached(src + j + 1);
+      chain = crypt_block<NR, AES_ENCRYPT>(xor4(p, chain), kw, sm, lc);
+      st_block(dst + j, chain);
+    }
+  }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(512, 1)
+cbc_decrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride, uint64_t nmsgs, uint64_t mblocks,
+                   const KeyWords kw) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  fill_tables<AES_DECRYPT>(smem);
+  __syncthreads();
+  const char* sm = reinterpret_cast<const char*>(smem);
+  const uint32_t lc = (threadIdx.x & 31u) * 4u;
+  const uint64_t total = nmsgs * mblocks;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const uint64_t msg = g / mblocks, j = g - msg * mblocks;
+    const uint4 c = ld_cached(in + g);
+    const uint4 prev = j ? ld_cached(in + g - 1) : ld_cached(ivs + (iv_stride ? msg : 0));
+    st_block(out + g, xor4(crypt_block<NR, AES_DECRYPT>(c, kw, sm, lc), prev));
+  }
+}
+
+using CbcKernel = void (*)(const uint4*, uint4*, const uint4*, int, uint64_t, uint64_t, const KeyWords);
+
+CbcKernel pick(int dir, int nr) {
+  if (dir == AES_ENCRYPT) return nr == 10 ? cbc_encrypt_kernel<10> : nr == 12 ? cbc_encrypt_kernel<12> : cbc_encrypt_kernel<14>;
+  return nr == 10 ? cbc_decrypt_kernel<10> : nr == 12 ? cbc_decrypt_kernel<12> : cbc_decrypt_kernel<14>;
+}
+
+}  // namespace
+}  // namespace aesgb
+
+using namespace aesgb;
+
+extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_ivs, int iv_per_msg, const void* d_in,
+                                    void* d_out, size_t nmsgs, size_t blocks_per_msg, int dir, void* cuda_stream) {
+  clear_error();
+  if (!schedule_ok(ks)) return set_error(AES_EINVAL, "invalid key schedule (nr must be 10, 12 or 14)");
+  if (dir != AES_ENCRYPT && dir != AES_DECRYPT) return set_error(AES_EINVAL, "dir must be AES_ENCRYPT or AES_DECRYPT");
+  if (iv_per_msg != 0 && iv_per_msg != 1) return set_error(AES_EINVAL, "iv_per_msg must be 0 or 1");
+  if (nmsgs == 0 || blocks_per_msg == 0) return AES_OK;
+  if (!d_in || !d_out || !d_ivs) return set_error(AES_EINVAL, "null buffer");
+  if ((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out) | reinterpret_cast<uintptr_t>(d_ivs)) & 15u)
+    return set_error(AES_EINVAL, "buffers must be 16-byte aligned");
+  if (blocks_per_msg > (SIZE_MAX >> 5) / nmsgs) return set_error(AES_EINVAL, "matrix too large");
+  const uintptr_t a = reinterpret_cast<uintptr_t>(d_in), b = reinterpret_cast<uintptr_t>(d_out);
+  const uintptr_t bytes = uintptr_t(nmsgs) * blocks_per_msg * 16u;
+  if (a != b && a < b + bytes && b < a + bytes)
+    return set_error(AES_EINVAL, "input and output overlap without being identical");
+  if (dir == AES_DECRYPT && a == b)
+    return set_error(AES_EINVAL, "CBC decryption cannot run in place (each block needs the previous ciphertext)");
+  const DeviceInfo* di = current_device_info();
+  if (!di) return AES_ECUDA;
+  // the kernel adds the IV itself: the schedule goes in without one
+  const KeyWords kw = dir == AES_ENCRYPT ? enc_key_words(*ks, nullptr) : dec_key_words(*ks, nullptr);
+  CbcKernel k = pick(dir, ks->nr);
+  const size_t smem = ttable_smem_bytes(dir);
+  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(CBC)");
+  unsigned threads = 512u;
+  uint64_t work = uint64_t(nmsgs) * blocks_per_msg;
+  if (dir == AES_ENCRYPT) {
+    // a lane per message: with few messages, spread the chains over all SMs (smaller CTAs)
+    // rather than packing them into a few
+    work = nmsgs;
+    const uint64_t per_sm = (work + di->sms - 1) / di->sms;
+    threads = per_sm >= 512 ? 512u : unsigned(((per_sm + 31) / 32) * 32);
+  }
+  const uint64_t want = (work + threads - 1) / threads;
+  const unsigned grid = unsigned(want < uint64_t(di->sms) ? want : uint64_t(di->sms));
+  k<<<grid, threads, smem, static_cast<cudaStream_t>(cuda_stream)>>>(
+      static_cast<const uint4*>(d_in), static_cast<uint4*>(d_out), static_cast<const uint4*>(d_ivs), iv_per_msg,
+      nmsgs, blocks_per_msg, kw);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "CBC kernel launch");
+  return AES_OK;
+}

@@ -1,0 +1,86 @@
+"""GPU parity of the paper's CBC mode over whole messages (Section II; App. A1, A4) against
+the oracle's per-message CBC (itself pinned to OpenSSL CBC).  Bit-exact."""
+import os
+
+import numpy as np
+import pytest
+
+import paper_1506_08503_gb300 as aes
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 4
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("key_bits", [128, 192, 256])
+@pytest.mark.parametrize("m", [1, 2, 17, 100])
+def test_paper_shape_128_messages_one_iv(aes_lib_ready, orc, key_bits, m):
+    # the paper's second workload shape: 128 messages of a given length, one repeated IV
+    rng = np.random.default_rng(70 + m + key_bits)
+    key = rng.integers(0, 256, key_bits // 8, dtype=np.uint8)
+    iv = rng.integers(0, 256, 16, dtype=np.uint8)
+    pt = rng.integers(0, 256, (128, 16 * m), dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes(), key_bits)
+    ct = aes.cbc(dev(pt), ks, dev(iv), "encrypt").cpu().numpy()
+    for i in range(128):
+        assert (ct[i] == orc.cbc_encrypt(key, iv, pt[i])).all(), i
+    back = aes.cbc(dev(ct), ks, dev(iv), "decrypt").cpu().numpy()
+    assert (back == pt).all()
+
+
+def test_iv_per_message_and_many_messages(aes_lib_ready, orc):
+    rng = np.random.default_rng(80)
+    n, m = 20011, 9
+    key = rng.integers(0, 256, 16, dtype=np.uint8)
+    ivs = rng.integers(0, 256, (n, 16), dtype=np.uint8)
+    pt = rng.integers(0, 256, (n, 16 * m), dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes())
+    ct = aes.cbc(dev(pt), ks, dev(ivs), "encrypt").cpu().numpy()
+    for i in list(range(0, n, 997)) + [n - 1]:
+        assert (ct[i] == orc.cbc_encrypt(key, ivs[i], pt[i])).all(), i
+    # decryption of arbitrary data matches the oracle too (not only round trips)
+    junk = rng.integers(0, 256, (n, 16 * m), dtype=np.uint8)
+    dj = aes.cbc(dev(junk), ks, dev(ivs), "decrypt").cpu().numpy()
+    for i in list(range(0, n, 1999)) + [n - 1]:
+        assert (dj[i] == orc.cbc_decrypt(key, ivs[i], junk[i])).all(), i
+    assert (aes.cbc(dev(ct), ks, dev(ivs), "decrypt").cpu().numpy() == pt).all()
+
+
+def test_long_single_message_and_in_place(aes_lib_ready, orc):
+    import torch
+
+    rng = np.random.default_rng(81)
+    key = rng.integers(0, 256, 32, dtype=np.uint8)
+    iv = rng.integers(0, 256, 16, dtype=np.uint8)
+    pt = rng.integers(0, 256, (1, 16 * 5000), dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes(), 256)
+    x = dev(pt)
+    aes.cbc(x, ks, dev(iv), "encrypt", out=x)  # encryption may run in place
+    torch.cuda.synchronize()
+    assert (x.cpu().numpy()[0] == orc.cbc_encrypt(key, iv, pt[0])).all()
+    with pytest.raises(aes.AesError) as ei:
+        aes.cbc(x, ks, dev(iv), "decrypt", out=x)
+    assert ei.value.status == aes.AES_EINVAL
+    y = aes.cbc(x, ks, dev(iv), "decrypt")
+    assert (y.cpu().numpy() == pt).all()
+
+
+def test_cbc_argument_checks(aes_lib_ready):
+    import torch
+
+    ks = aes.aes_key_expand(bytes(16))
+    x = torch.zeros((4, 64), dtype=torch.uint8, device="cuda")
+    iv = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    lib = aes.lib()
+    import ctypes
+
+    assert lib.aes_cbc_crypt(ctypes.byref(ks), iv.data_ptr(), 0, x.data_ptr(), x.data_ptr(), 0, 4, 0, None) == 0
+    assert lib.aes_cbc_crypt(ctypes.byref(ks), iv.data_ptr(), 2, x.data_ptr(), x.data_ptr(), 4, 4, 0, None) == aes.AES_EINVAL
+    assert lib.aes_cbc_crypt(ctypes.byref(ks), iv.data_ptr() + 8, 0, x.data_ptr(), x.data_ptr(), 4, 4, 0, None) == aes.AES_EINVAL
+    assert lib.aes_cbc_crypt(ctypes.byref(ks), None, 0, x.data_ptr(), x.data_ptr(), 4, 4, 0, None) == aes.AES_EINVAL
+    assert lib.aes_cbc_crypt(ctypes.byref(ks), iv.data_ptr(), 0, x.data_ptr(), x.data_ptr() + 16, 4, 4, 0, None) == aes.AES_EINVAL
