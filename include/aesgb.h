@@ -104,6 +104,24 @@ aes_status aes_crypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, const
 aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_ivs, int iv_per_msg, const void* d_in,
                          void* d_out, size_t nmsgs, size_t blocks_per_msg, int dir, void* cuda_stream);
 
+/* Counter mode, a follow-on the paper names as future work (Section V): block i becomes
+ * in_i xor Cipher(T + i), where T is the 16-byte initial counter block ctr0 (host pointer)
+ * read as a big-endian 128-bit integer and the sum is taken mod 2^128.  Encryption and
+ * decryption are the same call.  Buffer rules as aes_crypt_blocks (device, 16-byte aligned,
+ * in place allowed). */
+aes_status aes_ctr_crypt(const aes_key_schedule* ks, const uint8_t* ctr0, const void* d_in, void* d_out,
+                         size_t nblocks, void* cuda_stream);
+
+/* Equality query on a deterministically encrypted column (the encrypted-database use the
+ * paper motivates in Section I): under one key and IV, equal 16-byte records have equal
+ * ciphertexts, so the records equal to a query are those whose ciphertext equals the query's
+ * ciphertext `needle` (16 bytes, host).  Scans d_column (device, nrecords x 16 bytes, 16-byte
+ * aligned), writes the total number of matches to *d_count (device uint64, zeroed by the call)
+ * and the first min(count, max_matches) matching record indices to d_matches (device uint64,
+ * in no particular order).  Asynchronous on cuda_stream. */
+aes_status aes_scan_equal(const void* d_column, size_t nrecords, const uint8_t* needle, uint64_t* d_matches,
+                          size_t max_matches, uint64_t* d_count, void* cuda_stream);
+
 /* Same cipher on HOST buffers: the library copies the data to the device in 64 MiB chunks,
  * runs the kernel and copies the result back, overlapping the three on its own streams.
  *   h_in, h_out  host pointers (pinned memory gives full copy bandwidth; pageable works,
@@ -253,6 +271,7 @@ typedef struct {
   double p50_us, p99_us, max_us, mean_us; /* submit-to-completion latency of completed requests */
   double gbps;                            /* bytes_completed / (last completion - first submit) */
   double mean_batch;                      /* requests per launch */
+  double gbps_from_first_launch;          /* bytes_completed / (last completion - first launch) */
 } aes_server_stats;
 
 /* Starts a server on the current device over `pool` (which must outlive the server).  The

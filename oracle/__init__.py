@@ -75,6 +75,7 @@ def _declare(l: ctypes.CDLL) -> ctypes.CDLL:
         "oracle_decrypt_blocks": (i, [_U8P, i, _U8P, _U8P, _U8P, sz, i]),
         "oracle_cbc_encrypt": (None, [_U8P, i, _U8P, _U8P, _U8P, sz]),
         "oracle_cbc_decrypt": (None, [_U8P, i, _U8P, _U8P, _U8P, sz]),
+        "oracle_ctr_crypt": (None, [_U8P, i, _U8P, _U8P, _U8P, sz]),
     }
     for name, (res, args) in sig.items():
         f = getattr(l, name)
@@ -176,6 +177,14 @@ class Oracle:
         src = _u8(data).reshape(-1)
         out = np.empty_like(src)
         self.lib.oracle_cbc_decrypt(_p(rk), nr, _p(_u8(iv)), _p(src), _p(out), src.size // 16)
+        return out
+
+
+    def ctr_crypt(self, key, ctr0, data) -> np.ndarray:
+        rk, nr = self.key_expand(key)
+        src = _u8(data).reshape(-1)
+        out = np.empty_like(src)
+        self.lib.oracle_ctr_crypt(_p(rk), nr, _p(_u8(ctr0)), _p(src), _p(out), src.size // 16)
         return out
 
 

@@ -29,6 +29,9 @@
  *     InvShiftRows, InvSubBytes; then add round key 0 and the IV              [App. A4]
  *   - CBC chaining over the blocks of one message (the ciphertext of block j is the IV of
  *     block j+1)                                                     [Section II, App. A1, A4]
+ *   - counter mode, which the paper leaves to future work (Section V): block i is
+ *     P_i + Cipher(T + i), T the initial counter block read as a big-endian 128-bit integer
+ *     (the usual counter increment of the AES modes); pinned against OpenSSL's CTR
  *
  * Parity is pinned by the test suite (GF brute force, field and S-box invariants, the
  * paper's worked examples, and bit-exact agreement with OpenSSL's AES).
@@ -353,5 +356,20 @@ void oracle_cbc_decrypt(const uint8_t* rk, int nr, const uint8_t iv[16], const u
     memcpy(next, in + 16 * j, 16); /* in == out is allowed */
     oracle_decrypt_block(rk, nr, chain, in + 16 * j, out + 16 * j);
     memcpy(chain, next, 16);
+  }
+}
+
+/* Counter mode: out_i = in_i + Cipher(T + i), the counter block T a big-endian integer mod
+ * 2^128 (Section V names counter-based modes as future work; the increment is the standard
+ * one).  Encryption and decryption are the same operation. */
+void oracle_ctr_crypt(const uint8_t* rk, int nr, const uint8_t ctr0[16], const uint8_t* in, uint8_t* out,
+                      size_t nblocks) {
+  uint8_t ctr[16], ks[16];
+  memcpy(ctr, ctr0, 16);
+  for (size_t j = 0; j < nblocks; ++j) {
+    oracle_encrypt_block(rk, nr, NULL, ctr, ks);
+    for (int b = 0; b < 16; ++b) out[16 * j + b] = oracle_gf_add(in[16 * j + b], ks[b]);
+    for (int b = 15; b >= 0; --b) /* increment the 128-bit big-endian counter */
+      if (++ctr[b] != 0) break;
   }
 }

@@ -60,6 +60,10 @@ void oracle_cbc_encrypt(const uint8_t* rk, int nr, const uint8_t iv[16], const u
 void oracle_cbc_decrypt(const uint8_t* rk, int nr, const uint8_t iv[16], const uint8_t* in,
                         uint8_t* out, size_t nblocks);
 
+/* counter mode: out_i = in_i xor Cipher(ctr0 + i), ctr0 a big-endian 128-bit integer */
+void oracle_ctr_crypt(const uint8_t* rk, int nr, const uint8_t ctr0[16], const uint8_t* in, uint8_t* out,
+                      size_t nblocks);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,7 +78,8 @@ class aes_request(ctypes.Structure):
 class aes_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "queued", "inflight", "launches",
                                                 "bytes_completed")] + \
-               [(n, ctypes.c_double) for n in ("p50_us", "p99_us", "max_us", "mean_us", "gbps", "mean_batch")]
+               [(n, ctypes.c_double) for n in ("p50_us", "p99_us", "max_us", "mean_us", "gbps", "mean_batch",
+                                                "gbps_from_first_launch")]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -107,6 +108,8 @@ _SIGS: dict[str, tuple] = {
     "aes_crypt_blocks": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _I, _I, _VP]),
     "aes_crypt_host": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _I, _I, _VP]),
     "aes_cbc_crypt": (_I, [_KSP, _VP, _I, _VP, _VP, _SZ, _SZ, _I, _VP]),
+    "aes_ctr_crypt": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _VP]),
+    "aes_scan_equal": (_I, [_VP, _SZ, _U8P, _VP, _SZ, _VP, _VP]),
     "aes_crypt_batched_noalloc": (_I, [_KSP, ctypes.c_uint32, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "aes_keypool_create": (_I, [_SZ, ctypes.POINTER(_VP)]),
     "aes_keypool_load_keys": (_I, [_VP, ctypes.c_uint32, _SZ, _U8P, _I, _VP]),
@@ -250,6 +253,40 @@ def cbc(x, ks: aes_key_schedule, ivs, dir="encrypt", out=None, stream=None):
     aes_cbc_crypt(ks, ivs.data_ptr(), per_msg, x.data_ptr(), out.data_ptr(), x.shape[0], x.shape[1] // 16, dir,
                   stream)
     return out
+
+
+def aes_ctr_crypt(ks: aes_key_schedule, ctr0: bytes, d_in: int, d_out: int, nblocks: int, stream=None) -> None:
+    p, _keep = _bytes_ptr(ctr0)
+    _check(lib().aes_ctr_crypt(ctypes.byref(ks), p, d_in, d_out, nblocks, _stream_ptr(stream)))
+
+
+def ctr(x, ks: aes_key_schedule, ctr0: bytes, out=None, stream=None):
+    """Counter mode on a CUDA tensor of whole blocks (same call encrypts and decrypts)."""
+    import torch
+
+    n = _blocks_of(x)
+    if out is None:
+        out = torch.empty_like(x)
+    aes_ctr_crypt(ks, ctr0, x.data_ptr(), out.data_ptr(), n, stream)
+    return out
+
+
+def aes_scan_equal(d_column: int, nrecords: int, needle: bytes, d_matches: int, max_matches: int, d_count: int,
+                   stream=None) -> None:
+    p, _keep = _bytes_ptr(needle)
+    _check(lib().aes_scan_equal(d_column, nrecords, p, d_matches, max_matches, d_count, _stream_ptr(stream)))
+
+
+def find_equal(column, needle: bytes, max_matches: int = 1 << 20, stream=None):
+    """Indices (sorted) of the 16-byte records of the CUDA tensor `column` equal to `needle`."""
+    import torch
+
+    n = _blocks_of(column)
+    matches = torch.empty(max(1, max_matches), dtype=torch.int64, device=column.device)
+    count = torch.zeros(1, dtype=torch.int64, device=column.device)
+    aes_scan_equal(column.data_ptr(), n, needle, matches.data_ptr(), max_matches, count.data_ptr(), stream)
+    k = int(count.item())
+    return torch.sort(matches[: min(k, max_matches)]).values, k
 
 
 def aes_crypt_batched_noalloc(schedules, msgs, d_in: int, d_out: int, buf_bytes: int, stream=None) -> None:

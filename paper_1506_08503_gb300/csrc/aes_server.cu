@@ -7,8 +7,8 @@
 // memory allow, and starts them as ONE batched launch on that stream:
 //   host-sourced payloads are copied into the staging arena (or straight into a device
 //   destination), the batch graph runs the cipher in place or device-to-device, and host
-//   destinations are copied back; a host callback at the end of the stream marks the batch
-//   complete and wakes the thread.
+//   destinations are copied back; a host callback at the end of the stream marks the batch's
+//   requests complete, frees their staging and wakes the thread and any waiting poll.
 // Requests arriving while batches run are admitted into the next free stream's batch, so the
 // device works on several batches at once and nobody waits for a full drain.
 //
@@ -95,8 +95,7 @@ struct StreamSlot {
   cudaStream_t stream = nullptr;
   aes_batch* batch = nullptr;
   bool busy = false;
-  uint64_t first = 0, last = 0;    // the batch is the ticket range [first, last)
-  std::vector<BatchMsg> enc, dec;  // its descriptors (capacity reused)
+  uint64_t first = 0, last = 0;  // the batch is the ticket range [first, last)
 };
 
 struct DoneMsg {
@@ -124,8 +123,6 @@ struct aes_server {
   uint64_t mask = 0;
   uint64_t next_ticket = 1;    // next ticket to hand out
   uint64_t admit = 1;          // first ticket not admitted yet: the queue is [admit, next_ticket)
-  std::vector<int> finished_slots;  // posted by stream callbacks
-  std::vector<double> finished_time;
   uint64_t inflight = 0;
   bool stop = false;
   std::thread worker;
@@ -133,22 +130,27 @@ struct aes_server {
   // statistics
   std::vector<double> lat_us;
   uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, launched_reqs = 0, bytes_done = 0;
-  double t_first = 0, t_last = 0;
+  double t_first = 0, t_last = 0, t_first_launch = 0;
 
   Req& at(uint64_t t) { return ring[t & mask]; }
 };
 
 namespace {
 
+// Forward declaration: the callback retires its batch itself.
+void retire(aes_server* s, StreamSlot& sl, double t, int state);
+
+// Runs on a CUDA driver thread once everything queued for the batch has finished (no CUDA
+// calls here): marks the batch's requests done, frees their staging and wakes everyone.
 void CUDART_CB on_batch_done(void* p) {
   DoneMsg* m = static_cast<DoneMsg*>(p);
   aes_server* s = m->s;
   const double t = now_s();
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    s->finished_slots.push_back(m->slot);
-    s->finished_time.push_back(t);
+    retire(s, s->slots[m->slot], t, AES_REQ_DONE);
   }
+  s->cv_done.notify_all();
   s->cv_work.notify_one();
 }
 
@@ -172,44 +174,42 @@ void retire(aes_server* s, StreamSlot& sl, double t, int state) {
   sl.busy = false;
 }
 
-// Issues the tickets [sl.first, sl.last) on slot i (mu NOT held; the batch owns its slots).
+// Issues the tickets [sl.first, sl.last) on slot i (mu NOT held; the batch owns its ring
+// slots until its callback retires them).
 aes_status issue(aes_server* s, int i) {
   StreamSlot& sl = s->slots[i];
   cudaStream_t st = sl.stream;
   cudaError_t e;
   if (s->cfg.fail_every && s->launches % s->cfg.fail_every == 0)  // launches n, 2n, 3n, ...: fake a failure
     return set_error(AES_ECUDA, "injected launch failure (fail_every = %u)", s->cfg.fail_every);
-  std::vector<BatchMsg>& enc = sl.enc;
-  std::vector<BatchMsg>& dec = sl.dec;
-  enc.clear();
-  dec.clear();
+  // pass 1: host payloads go to the device, and the batch is counted per direction
+  size_t nenc = 0, ndec = 0;
   for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
     const Req& q = s->at(tk);
     const aes_request& r = q.r;
-    uint64_t in_addr, out_addr;
-    if (r.src_on_device && r.dst_on_device) {
-      in_addr = reinterpret_cast<uint64_t>(r.src);
-      out_addr = reinterpret_cast<uint64_t>(r.dst);
-    } else if (!r.src_on_device && r.dst_on_device) {
-      if ((e = cudaMemcpyAsync(r.dst, r.src, r.length, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_error(e, "H2D");
-      in_addr = out_addr = reinterpret_cast<uint64_t>(r.dst);
-    } else {
-      uint8_t* stage = s->arena_base + q.stage_off;
-      if (r.src_on_device) in_addr = reinterpret_cast<uint64_t>(r.src);
-      else {
-        if ((e = cudaMemcpyAsync(stage, r.src, r.length, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_error(e, "H2D");
-        in_addr = reinterpret_cast<uint64_t>(stage);
-      }
-      out_addr = reinterpret_cast<uint64_t>(stage);
+    if (!r.src_on_device) {
+      void* to = r.dst_on_device ? r.dst : static_cast<void*>(s->arena_base + q.stage_off);
+      if ((e = cudaMemcpyAsync(to, r.src, r.length, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_error(e, "H2D");
     }
-    const BatchMsg d{r.key_idx, 0u, in_addr / 16, out_addr / 16, r.length / 16};
-    (r.dir == AES_ENCRYPT ? enc : dec).push_back(d);
+    (r.dir == AES_ENCRYPT ? nenc : ndec)++;
   }
+  // pass 2 (inside the batch launch): descriptors written straight into the pinned staging.
+  // A device destination is the output; a host destination is served from the staging slot,
+  // which also holds the input when the source was on the host.
   auto fill = [&](BatchMsg* em, BatchMsg* dm) {
-    if (!enc.empty()) std::memcpy(em, enc.data(), enc.size() * sizeof(BatchMsg));
-    if (!dec.empty()) std::memcpy(dm, dec.data(), dec.size() * sizeof(BatchMsg));
+    size_t ie = 0, id = 0;
+    for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
+      const Req& q = s->at(tk);
+      const aes_request& r = q.r;
+      const uint64_t stage = reinterpret_cast<uint64_t>(s->arena_base + q.stage_off);
+      const uint64_t out_addr = r.dst_on_device ? reinterpret_cast<uint64_t>(r.dst) : stage;
+      const uint64_t in_addr = r.src_on_device ? reinterpret_cast<uint64_t>(r.src) : out_addr;
+      const BatchMsg d{r.key_idx, 0u, in_addr / 16, out_addr / 16, r.length / 16};
+      if (r.dir == AES_ENCRYPT) em[ie++] = d;
+      else dm[id++] = d;
+    }
   };
-  aes_status rc = batch_launch_descs(sl.batch, enc.size(), dec.size(), fill, 0, 0, st);
+  aes_status rc = batch_launch_descs(sl.batch, nenc, ndec, fill, 0, 0, st);
   if (rc != AES_OK) return rc;
   for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
     const Req& q = s->at(tk);
@@ -225,14 +225,6 @@ void worker_main(aes_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
-    // 1. retire finished batches
-    for (size_t k = 0; k < s->finished_slots.size(); ++k)
-      retire(s, s->slots[s->finished_slots[k]], s->finished_time[k], AES_REQ_DONE);
-    if (!s->finished_slots.empty()) {
-      s->finished_slots.clear();
-      s->finished_time.clear();
-      s->cv_done.notify_all();
-    }
     bool any_busy = false;
     int free_slot = -1;
     for (size_t i = 0; i < s->slots.size(); ++i) {
@@ -279,6 +271,7 @@ void worker_main(aes_server* s) {
     sl.busy = true;
     sl.first = first;
     sl.last = t;
+    if (s->launches == 0 || s->t_first_launch == 0) s->t_first_launch = now_s();
     ++s->launches;
     s->launched_reqs += t - first;
     lk.unlock();
@@ -492,6 +485,8 @@ aes_status aes_server_stats_get(aes_server* s, aes_server_stats* out) {
     out->bytes_completed = s->bytes_done;
     out->mean_batch = s->launches ? double(s->launched_reqs) / double(s->launches) : 0.0;
     out->gbps = (s->t_last > s->t_first && s->t_first > 0) ? s->bytes_done / (s->t_last - s->t_first) / 1e9 : 0.0;
+    out->gbps_from_first_launch = (s->t_last > s->t_first_launch && s->t_first_launch > 0)
+                                      ? s->bytes_done / (s->t_last - s->t_first_launch) / 1e9 : 0.0;
     lat = s->lat_us;
   }
   if (!lat.empty()) {
@@ -516,7 +511,7 @@ aes_status aes_server_stats_reset(aes_server* s) {
   std::lock_guard<std::mutex> lk(s->mu);
   s->lat_us.clear();
   s->submitted = s->completed = s->failed = s->launches = s->launched_reqs = s->bytes_done = 0;
-  s->t_first = s->t_last = 0;
+  s->t_first = s->t_last = s->t_first_launch = 0;
   return AES_OK;
 }
 

@@ -179,3 +179,24 @@ def test_round_trip_random(orc):
         iv = rng.integers(0, 256, 16, dtype=np.uint8)
         data = rng.integers(0, 256, 16 * 64, dtype=np.uint8)
         assert (orc.decrypt_blocks(key, orc.encrypt_blocks(key, data, iv=iv), iv=iv) == data).all()
+
+
+def openssl_ctr(key: bytes, ctr0: bytes, data: bytes) -> bytes:
+    c = _openssl()
+    op = c.Cipher(c.algorithms.AES(key), c.modes.CTR(ctr0)).encryptor()
+    return op.update(data) + op.finalize()
+
+
+@pytest.mark.parametrize("key_bits", [128, 256])
+def test_ctr_matches_openssl_including_counter_wrap(orc, key_bits):
+    rng = np.random.default_rng(23 + key_bits)
+    for wrap in (False, True):
+        key = rng.integers(0, 256, key_bits // 8, dtype=np.uint8)
+        ctr0 = rng.integers(0, 256, 16, dtype=np.uint8)
+        if wrap:  # the low 64 bits overflow into the high half, and the whole block wraps
+            ctr0[:] = 0xFF
+            ctr0[0] = 0x7F
+        data = rng.integers(0, 256, 16 * 37, dtype=np.uint8)
+        ct = orc.ctr_crypt(key, ctr0, data)
+        assert ct.tobytes() == openssl_ctr(key.tobytes(), ctr0.tobytes(), data.tobytes())
+        assert (orc.ctr_crypt(key, ctr0, ct) == data).all()
