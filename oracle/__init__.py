@@ -76,6 +76,9 @@ def _declare(l: ctypes.CDLL) -> ctypes.CDLL:
         "oracle_cbc_encrypt": (None, [_U8P, i, _U8P, _U8P, _U8P, sz]),
         "oracle_cbc_decrypt": (None, [_U8P, i, _U8P, _U8P, _U8P, sz]),
         "oracle_ctr_crypt": (None, [_U8P, i, _U8P, _U8P, _U8P, sz]),
+        "oracle_gf128_mul": (None, [_U8P, _U8P, _U8P]),
+        "oracle_ghash": (None, [_U8P, _U8P, sz, _U8P]),
+        "oracle_gcm_crypt": (None, [_U8P, i, _U8P, _U8P, sz, _U8P, _U8P, sz, i, _U8P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(l, name)
@@ -179,13 +182,41 @@ class Oracle:
         self.lib.oracle_cbc_decrypt(_p(rk), nr, _p(_u8(iv)), _p(src), _p(out), src.size // 16)
         return out
 
-
     def ctr_crypt(self, key, ctr0, data) -> np.ndarray:
         rk, nr = self.key_expand(key)
         src = _u8(data).reshape(-1)
         out = np.empty_like(src)
         self.lib.oracle_ctr_crypt(_p(rk), nr, _p(_u8(ctr0)), _p(src), _p(out), src.size // 16)
         return out
+
+    # Galois/Counter Mode
+    def gf128_mul(self, x, y) -> np.ndarray:
+        z = np.empty(16, dtype=np.uint8)
+        self.lib.oracle_gf128_mul(_p(_u8(x)), _p(_u8(y)), _p(z))
+        return z
+
+    def ghash(self, h, data) -> np.ndarray:
+        src = _u8(data).reshape(-1)
+        if src.size % 16:
+            raise ValueError("GHASH input must be whole 16-byte blocks")
+        y = np.empty(16, dtype=np.uint8)
+        self.lib.oracle_ghash(_p(_u8(h)), _p(src), src.size // 16, _p(y))
+        return y
+
+    def gcm_crypt(self, key, iv, data, aad=b"", decrypt: bool = False) -> tuple[np.ndarray, np.ndarray]:
+        """(output bytes, tag); the data and AAD may have any length."""
+        rk, nr = self.key_expand(key)
+        ivv = _u8(iv)
+        if ivv.size != 12:
+            raise ValueError("the GCM oracle takes 96-bit IVs")
+        src = _u8(data).reshape(-1)
+        a = _u8(aad).reshape(-1)
+        out = np.empty_like(src)
+        tag = np.empty(16, dtype=np.uint8)
+        self.lib.oracle_gcm_crypt(_p(rk), nr, _p(ivv), _p(a) if a.size else None, a.size,
+                                  _p(src) if src.size else None, _p(out) if src.size else None, src.size,
+                                  int(decrypt), _p(tag))
+        return out, tag
 
 
 _default: Oracle | None = None

@@ -32,6 +32,11 @@
  *   - counter mode, which the paper leaves to future work (Section V): block i is
  *     P_i + Cipher(T + i), T the initial counter block read as a big-endian 128-bit integer
  *     (the usual counter increment of the AES modes); pinned against OpenSSL's CTR
+ *   - the Galois/Counter Mode, the counter-based authenticated mode that Section V names as
+ *     future work.  The paper does not define it; this follows NIST SP 800-38D: the
+ *     GF(2^128) product bit by bit (its Algorithm 1), GHASH as Horner's rule (Algorithm 2),
+ *     and GCM with a 96-bit IV (Algorithms 4 and 5: J0 = IV || 0^31 || 1, data counters
+ *     from inc32(J0), tag = Cipher(J0) + GHASH(A, C, lengths)); pinned against OpenSSL's GCM
  *
  * Parity is pinned by the test suite (GF brute force, field and S-box invariants, the
  * paper's worked examples, and bit-exact agreement with OpenSSL's AES).
@@ -372,4 +377,79 @@ void oracle_ctr_crypt(const uint8_t* rk, int nr, const uint8_t ctr0[16], const u
     for (int b = 15; b >= 0; --b) /* increment the 128-bit big-endian counter */
       if (++ctr[b] != 0) break;
   }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Galois/Counter Mode (NIST SP 800-38D; Section V of the paper names it as future work)  */
+/* ------------------------------------------------------------------------------------ */
+
+/* Product in GF(2^128), one bit of x at a time (SP 800-38D Algorithm 1).  v runs through
+ * y * x^i: multiplying by x moves every coefficient one bit towards the end of the block,
+ * and a coefficient that leaves x^127 comes back as x^7 + x^2 + x + 1, which is 0xE1 in
+ * byte 0. */
+void oracle_gf128_mul(const uint8_t x[16], const uint8_t y[16], uint8_t z[16]) {
+  uint8_t v[16], acc[16];
+  memset(acc, 0, 16);
+  memcpy(v, y, 16);
+  for (int i = 0; i < 128; ++i) {
+    if ((x[i / 8] >> (7 - i % 8)) & 1)
+      for (int k = 0; k < 16; ++k) acc[k] ^= v[k];
+    const int out = v[15] & 1;
+    for (int k = 15; k > 0; --k) v[k] = (uint8_t)((v[k] >> 1) | (v[k - 1] << 7));
+    v[0] >>= 1;
+    if (out) v[0] ^= 0xE1;
+  }
+  memcpy(z, acc, 16);
+}
+
+/* GHASH (SP 800-38D Algorithm 2): Y_i = (Y_{i-1} + X_i) * H from Y_0 = 0. */
+void oracle_ghash(const uint8_t h[16], const uint8_t* x, size_t nblocks, uint8_t y[16]) {
+  uint8_t acc[16];
+  memset(acc, 0, 16);
+  for (size_t j = 0; j < nblocks; ++j) {
+    for (int k = 0; k < 16; ++k) acc[k] ^= x[16 * j + k];
+    oracle_gf128_mul(acc, h, acc);
+  }
+  memcpy(y, acc, 16);
+}
+
+/* One GHASH step over a block that may be short: the missing bytes count as zero. */
+static void ghash_step(uint8_t acc[16], const uint8_t h[16], const uint8_t* blk, size_t nbytes) {
+  for (size_t k = 0; k < nbytes; ++k) acc[k] ^= blk[k];
+  oracle_gf128_mul(acc, h, acc);
+}
+
+/* GCM with a 96-bit IV (SP 800-38D Algorithms 4 and 5).  H = Cipher(0^128); J0 = IV || 0^31
+ * || 1; data block j is XORed with Cipher(J0 with its last 32 bits set to 2 + j mod 2^32);
+ * the hash runs over the AAD and the ciphertext, each zero-padded to whole blocks, then the
+ * block [64-bit bit length of AAD || 64-bit bit length of the ciphertext]; the tag is
+ * Cipher(J0) + that hash. */
+void oracle_gcm_crypt(const uint8_t* rk, int nr, const uint8_t iv[12], const uint8_t* aad, size_t aad_len,
+                      const uint8_t* in, uint8_t* out, size_t len, int decrypt, uint8_t tag[16]) {
+  uint8_t h[16], j0[16], ctr[16], ks[16], acc[16], blk[16];
+  memset(h, 0, 16);
+  oracle_encrypt_block(rk, nr, NULL, h, h);
+  memcpy(j0, iv, 12);
+  j0[12] = 0; j0[13] = 0; j0[14] = 0; j0[15] = 1;
+  memset(acc, 0, 16);
+  for (size_t off = 0; off < aad_len; off += 16)
+    ghash_step(acc, h, aad + off, aad_len - off < 16 ? aad_len - off : 16);
+  memcpy(ctr, j0, 12);
+  for (size_t j = 0; 16 * j < len; ++j) {
+    const size_t off = 16 * j, nb = len - off < 16 ? len - off : 16;
+    const uint32_t c = (uint32_t)(2u + (uint32_t)j); /* inc32 wraps mod 2^32 */
+    ctr[12] = (uint8_t)(c >> 24); ctr[13] = (uint8_t)(c >> 16); ctr[14] = (uint8_t)(c >> 8); ctr[15] = (uint8_t)c;
+    oracle_encrypt_block(rk, nr, NULL, ctr, ks);
+    memcpy(blk, in + off, nb); /* the ciphertext of a decryption, before in == out overwrites it */
+    for (size_t k = 0; k < nb; ++k) out[off + k] = oracle_gf_add(in[off + k], ks[k]);
+    ghash_step(acc, h, decrypt ? blk : out + off, nb);
+  }
+  const uint64_t abits = (uint64_t)aad_len * 8u, cbits = (uint64_t)len * 8u;
+  for (int k = 0; k < 8; ++k) {
+    blk[k] = (uint8_t)(abits >> (56 - 8 * k));
+    blk[8 + k] = (uint8_t)(cbits >> (56 - 8 * k));
+  }
+  ghash_step(acc, h, blk, 16);
+  oracle_encrypt_block(rk, nr, NULL, j0, ks);
+  for (int k = 0; k < 16; ++k) tag[k] = (uint8_t)(ks[k] ^ acc[k]);
 }

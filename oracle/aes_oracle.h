@@ -64,6 +64,16 @@ void oracle_cbc_decrypt(const uint8_t* rk, int nr, const uint8_t iv[16], const u
 void oracle_ctr_crypt(const uint8_t* rk, int nr, const uint8_t ctr0[16], const uint8_t* in, uint8_t* out,
                       size_t nblocks);
 
+/* GF(2^128) of the Galois/Counter Mode (NIST SP 800-38D): coefficient of x^i = bit i counted
+ * from the most significant bit of byte 0, reduced by x^128 + x^7 + x^2 + x + 1 */
+void oracle_gf128_mul(const uint8_t x[16], const uint8_t y[16], uint8_t z[16]);
+/* GHASH_H over nblocks whole blocks: Y_0 = 0, Y_i = (Y_{i-1} + X_i) * H */
+void oracle_ghash(const uint8_t h[16], const uint8_t* x, size_t nblocks, uint8_t y[16]);
+/* AES-GCM with a 96-bit IV; decrypt != 0 hashes `in` (the ciphertext) instead of `out`.
+ * Writes len bytes to out and the 16-byte tag.  in == out is allowed. */
+void oracle_gcm_crypt(const uint8_t* rk, int nr, const uint8_t iv[12], const uint8_t* aad, size_t aad_len,
+                      const uint8_t* in, uint8_t* out, size_t len, int decrypt, uint8_t tag[16]);
+
 #ifdef __cplusplus
 }
 #endif
