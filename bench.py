@@ -297,6 +297,32 @@ def measure_cbc(aes, torch, dev) -> dict:
     return {"mode": "CBC over whole messages, AES-128, one IV per message", "rows": rows}
 
 
+def measure_small_latency(aes, torch, dev) -> dict:
+    """The oracle-sized case: 4096 blocks (64 KiB, seed 0) encrypted then decrypted, one call at a
+    time on an idle GPU; this fits in L2 and is bound by launch latency, so it is reported in
+    microseconds (median over 200 calls, CUDA events around each call)."""
+    w = workloads.plain(0, 4096)
+    ks = aes.aes_key_expand(w.key.tobytes())
+    x = torch.from_numpy(w.data).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for d, src, dst in (("encrypt", x, y), ("decrypt", y, x)):
+        times = []
+        for k in range(210):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            aes.aes_crypt_blocks(ks, None, src.data_ptr(), dst.data_ptr(), 4096, d, "ttable")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 10:
+                times.append(e0.elapsed_time(e1) * 1e3)
+        out[d + "_us_median"] = statistics.median(times)
+    out["workload"] = "4096 blocks (64 KiB), AES-128, seed 0"
+    return out
+
+
 def measure_followons(aes, torch, dev, x, n: int, key: bytes) -> dict:
     """Counter mode over the benchmark's 1 GiB buffer, and an equality scan of a 10^7-record
     encrypted sensor column (160 MB, read once: an HBM-bound kernel, reported against the
@@ -536,6 +562,7 @@ def run_ours(args):
     followons = None
     if not args.no_followons and rank == 0:
         followons = measure_followons(aes, torch, dev, x, n, key)
+        followons["small_4096_blocks"] = measure_small_latency(aes, torch, dev)
 
     cbc = None
     if not args.no_cbc and rank == 0:

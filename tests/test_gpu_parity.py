@@ -158,10 +158,48 @@ def test_sensor_records(aes, orc, cuda, key_name):
     pt = aes.decrypt(ct, ks)
     torch.cuda.synchronize()
     assert torch.equal(pt, x)
-    # deterministic encryption: equal records give equal ciphertexts (equality queries work)
-    rec = col.records.reshape(-1, 16)
-    dup = np.flatnonzero(rec[:, 8:].view("<i8").ravel() == rec[0, 8:].view("<i8")[0])[:2]
-    if dup.size == 2:
-        c = ct.view(-1, 16)[torch.from_numpy(dup).cuda()].cpu().numpy()
-        # timestamps differ, so the blocks differ; only identical 16-byte records collide
-        assert not (c[0] == c[1]).all()
+
+
+def test_buffer_beyond_4gib(aes, orc, cuda):
+    """2^28 + 1027 blocks (just over 4 GiB): block indices pass 2^28 and byte offsets pass 2^32,
+    so 32-bit index arithmetic anywhere would show.  Plain, batched and counter-mode paths."""
+    import torch
+
+    n = (1 << 28) + 1027
+    g = torch.Generator(device="cuda").manual_seed(28)
+    x = torch.randint(0, 256, (n * 16,), dtype=torch.uint8, device="cuda", generator=g)
+    key = np.arange(16, dtype=np.uint8) * 7
+    ks = aes.aes_key_expand(key.tobytes())
+    idx = np.array([0, 1, (1 << 28) - 1, 1 << 28, (1 << 28) + 1, n - 2, n - 1] +
+                   list(np.random.default_rng(3).integers(0, n, 64)), dtype=np.int64)
+    ti = torch.from_numpy(idx).cuda()
+    before = x.view(-1, 16)[ti].cpu().numpy().reshape(-1)
+    aes.encrypt(x, ks, out=x)  # in place: 4 GiB is enough memory for this test
+    got = x.view(-1, 16)[ti].cpu().numpy().reshape(-1)
+    assert (got == orc.encrypt_blocks(key, before, threads=THREADS)).all()
+    aes.decrypt(x, ks, out=x)
+    assert (x.view(-1, 16)[ti].cpu().numpy().reshape(-1) == before).all()
+    # batched: messages placed past the 4 GiB mark, each with its own key
+    with aes.KeyPool(3) as pool:
+        keys = np.stack([key, key[::-1].copy(), key ^ 0x5A])
+        pool.load_keys(0, keys, 128)
+        # the buffer ends 1027 blocks past 2^32 bytes; the three messages do not overlap
+        offs = [(1 << 32) - 16 * 5, (1 << 32) + 16 * 10, 16 * (n - 300)]
+        msgs = np.zeros(3, dtype=aes.msg_dtype())
+        msgs["key_idx"], msgs["offset"], msgs["length"] = [0, 1, 2], offs, [16 * 10, 16 * 700, 16 * 300]
+        src = [x[o:o + int(L)].cpu().numpy() for o, L in zip(offs, msgs["length"])]
+        aes.aes_crypt_batched(pool, msgs, x.data_ptr(), x.data_ptr(), n * 16)
+        torch.cuda.synchronize()
+        for k, (o, L) in enumerate(zip(offs, msgs["length"])):
+            assert (x[o:o + int(L)].cpu().numpy() == orc.encrypt_blocks(keys[k], src[k], threads=THREADS)).all()
+    # counter mode over the whole buffer: blocks past index 2^28 use counters past 2^28
+    ctr0 = bytes(16)
+    before = x.view(-1, 16)[ti].cpu().numpy()
+    aes.ctr(x, ks, ctr0, out=x)
+    got = x.view(-1, 16)[ti].cpu().numpy()
+    for j, i in enumerate(idx):
+        c = int(i).to_bytes(16, "big")
+        ksb = orc.encrypt_blocks(key, np.frombuffer(c, dtype=np.uint8))
+        assert (got[j] == (before[j] ^ ksb)).all(), i
+    del x
+    torch.cuda.empty_cache()
