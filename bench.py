@@ -324,7 +324,7 @@ def measure_small_latency(aes, torch, dev) -> dict:
 
 
 def measure_followons(aes, torch, dev, x, n: int, key: bytes) -> dict:
-    """Counter mode over the benchmark's 1 GiB buffer, and an equality scan of a 10^7-record
+    """Counter mode and GCM over the benchmark's 1 GiB buffer, and an equality scan of a 10^7-record
     encrypted sensor column (160 MB, read once: an HBM-bound kernel, reported against the
     measured copy bandwidth as read bytes per second)."""
     stream = torch.cuda.current_stream()
@@ -352,7 +352,24 @@ def measure_followons(aes, torch, dev, x, n: int, key: bytes) -> dict:
     ms_scan = timed(lambda: aes.aes_scan_equal(enc.data_ptr(), 10_000_000, needle, matches.data_ptr(), 1024,
                                                count.data_ptr()), 20)
     scan_gbs = 160e6 / (ms_scan / 1e3) / 1e9
+    # GCM over the same 1 GiB (16 KiB of AAD), each call = set-up, data pass and combine kernels
+    iv = bytes(range(12))
+    aad = torch.randint(0, 256, (16384,), dtype=torch.uint8, device=dev)
+    work = torch.empty(aes.aes_gcm_workspace_bytes(), dtype=torch.uint8, device=dev)
+    tag = torch.empty(16, dtype=torch.uint8, device=dev)
+
+    def gcm_call(d, m):
+        aes.aes_gcm_crypt(ks, iv, aad.data_ptr(), aad.numel(), x.data_ptr(), y.data_ptr(), m * 16, d, tag.data_ptr(),
+                          work.data_ptr(), work.numel())
+
+    ms_gcm_enc = timed(lambda: gcm_call("encrypt", n), 10)
+    ms_gcm_dec = timed(lambda: gcm_call("decrypt", n), 10)
+    us_gcm_small = timed(lambda: gcm_call("encrypt", 4096), 50) * 1e3
     return {"ctr_1GiB_gbs": n * 16 / (ms_ctr / 1e3) / 1e9,
+            "gcm_1GiB_encrypt_gbs": n * 16 / (ms_gcm_enc / 1e3) / 1e9,
+            "gcm_1GiB_decrypt_gbs": n * 16 / (ms_gcm_dec / 1e3) / 1e9,
+            "gcm_4096_blocks_us": us_gcm_small,
+            "gcm_note": "AES-128-GCM, 96-bit IV, 16 KiB AAD; 3 launches per call (set-up, data pass, combine)",
             "scan_1e7_records_gbs": scan_gbs, "scan_ms": ms_scan,
             "scan_frac_of_measured_copy_bw": scan_gbs / 6774.2,
             "note": "scan reads 16 B per record once; L2 (129 MB) holds part of the 160 MB column between repetitions"}

@@ -112,6 +112,30 @@ aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_ivs, int iv_p
 aes_status aes_ctr_crypt(const aes_key_schedule* ks, const uint8_t* ctr0, const void* d_in, void* d_out,
                          size_t nblocks, void* cuda_stream);
 
+/* AES-GCM, the counter-based authenticated mode that Section V of the paper names as future
+ * work; the paper does not define it, so this follows NIST SP 800-38D with a 96-bit IV.
+ * Data block j is XORed with Cipher(IV || 2 + j mod 2^32) (the last 32 bits count, big-endian,
+ * from J0 = IV || 0^31 || 1), and the 16-byte tag is Cipher(J0) + GHASH_H over the AAD and
+ * the ciphertext (each zero-padded to whole blocks) and the two bit lengths, H = Cipher(0).
+ *   ks         any schedule from aes_key_expand (AES-128/192/256)
+ *   iv, iv_len host IV; iv_len must be 12 (other IV lengths are not supported: AES_EINVAL)
+ *   d_aad      device, aad_len bytes (any length up to 64 GiB, 16-byte aligned pointer),
+ *              authenticated, not encrypted; may be NULL when aad_len is 0
+ *   d_in/d_out device, nbytes bytes (any length up to (2^32 - 2) * 16), 16-byte aligned;
+ *              in place allowed, partial overlap is AES_EINVAL; d_out must not overlap d_aad
+ *   dir        AES_ENCRYPT hashes the output, AES_DECRYPT hashes the input (the ciphertext)
+ *   d_tag      device, 16 bytes, any alignment: receives the tag.  On decryption it is the
+ *              tag computed from the ciphertext: the caller compares it with the received tag
+ *              before trusting the plaintext
+ *   d_work     device workspace of at least aes_gcm_workspace_bytes() bytes, 16-byte aligned,
+ *              owned by the caller; calls that share a workspace must be ordered on one
+ *              stream, and it must not overlap any other buffer
+ * Three kernel launches on cuda_stream (set-up, data pass, combine); asynchronous. */
+size_t aes_gcm_workspace_bytes(void);
+aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* iv, size_t iv_len, const void* d_aad,
+                         size_t aad_len, const void* d_in, void* d_out, size_t nbytes, int dir, uint8_t* d_tag,
+                         void* d_work, size_t work_bytes, void* cuda_stream);
+
 /* Equality query on a deterministically encrypted column (the encrypted-database use the
  * paper motivates in Section I): under one key and IV, equal 16-byte records have equal
  * ciphertexts, so the records equal to a query are those whose ciphertext equals the query's

@@ -110,6 +110,8 @@ _SIGS: dict[str, tuple] = {
     "aes_cbc_crypt": (_I, [_KSP, _VP, _I, _VP, _VP, _SZ, _SZ, _I, _VP]),
     "aes_ctr_crypt": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _VP]),
     "aes_scan_equal": (_I, [_VP, _SZ, _U8P, _VP, _SZ, _VP, _VP]),
+    "aes_gcm_workspace_bytes": (_SZ, []),
+    "aes_gcm_crypt": (_I, [_KSP, _U8P, _SZ, _VP, _SZ, _VP, _VP, _SZ, _I, _VP, _VP, _SZ, _VP]),
     "aes_crypt_batched_noalloc": (_I, [_KSP, ctypes.c_uint32, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "aes_keypool_create": (_I, [_SZ, ctypes.POINTER(_VP)]),
     "aes_keypool_load_keys": (_I, [_VP, ctypes.c_uint32, _SZ, _U8P, _I, _VP]),
@@ -269,6 +271,37 @@ def ctr(x, ks: aes_key_schedule, ctr0: bytes, out=None, stream=None):
         out = torch.empty_like(x)
     aes_ctr_crypt(ks, ctr0, x.data_ptr(), out.data_ptr(), n, stream)
     return out
+
+
+def aes_gcm_workspace_bytes() -> int:
+    return int(lib().aes_gcm_workspace_bytes())
+
+
+def aes_gcm_crypt(ks: aes_key_schedule, iv: bytes, d_aad: int, aad_len: int, d_in: int, d_out: int, nbytes: int,
+                  dir, d_tag: int, d_work: int, work_bytes: int, stream=None) -> None:
+    p, _keep = _bytes_ptr(iv)
+    _check(lib().aes_gcm_crypt(ctypes.byref(ks), p, len(iv), d_aad, aad_len, d_in, d_out, nbytes, _dir(dir), d_tag,
+                               d_work, work_bytes, _stream_ptr(stream)))
+
+
+def gcm(x, ks: aes_key_schedule, iv: bytes, aad=None, dir="encrypt", out=None, stream=None):
+    """AES-GCM on a contiguous CUDA uint8 tensor of any length; returns (output, 16-byte tag
+    tensor on the device).  On decryption the tag is the one computed from `x`: compare it
+    with the received tag before using the output."""
+    import torch
+
+    if x.dtype != torch.uint8 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA uint8 tensor")
+    if out is None:
+        out = torch.empty_like(x)
+    tag = torch.empty(16, dtype=torch.uint8, device=x.device)
+    work = torch.empty(aes_gcm_workspace_bytes(), dtype=torch.uint8, device=x.device)
+    a_ptr, a_len = (aad.data_ptr(), aad.numel()) if aad is not None and aad.numel() else (None, 0)
+    aes_gcm_crypt(ks, iv, a_ptr, a_len, x.data_ptr() if x.numel() else None, out.data_ptr() if x.numel() else None,
+                  x.numel(), dir, tag.data_ptr(), work.data_ptr(), work.numel(), stream)
+    if isinstance(stream, torch.cuda.Stream):  # the workspace is freed here, still in use there
+        work.record_stream(stream)
+    return out, tag
 
 
 def aes_scan_equal(d_column: int, nrecords: int, needle: bytes, d_matches: int, max_matches: int, d_count: int,

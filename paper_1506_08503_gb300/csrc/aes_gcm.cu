@@ -1,0 +1,443 @@
+// aes_gcm.cu -- AES-GCM (Galois/Counter Mode, NIST SP 800-38D) with 96-bit IVs.
+//
+// Section V of the paper names counter-based authenticated modes (GCM) as future work.  GCM
+// encrypts like counter mode -- data block j is XORed with the cipher of J0 = IV || 0^31 || 1
+// whose last 32 bits are replaced by 2 + j mod 2^32 -- and authenticates with GHASH, a
+// polynomial in H = Cipher(0^128) over GF(2^128) modulo x^128 + x^7 + x^2 + x + 1:
+//     S = X_1 H^m + X_2 H^(m-1) + ... + X_m H,    tag = Cipher(J0) + S,
+// where X runs over the AAD and the ciphertext (each zero-padded to whole blocks) and a last
+// block holding the two lengths in bits.  Coefficient of x^i = bit i of the block counted
+// from the most significant bit of byte 0.
+//
+// GHASH is a serial Horner chain; here the sum is split instead.  With T threads (512 per
+// CTA) and the n hashed blocks right-aligned in K*T positions (zeros in front), thread t
+// takes positions t, t + T, t + 2T, ... and runs Horner's rule with the fixed multiplier
+// Q = H^T, giving Y_t = sum_k X_(t+kT) Q^(K-1-k).  Then
+//     sum_i X_i H^(n-i) = H * sum_t Y_t H^(T-1-t),
+// and the last sum is a binary tree whose level j multiplies by H^(2^j): five levels between
+// the lanes of a warp (shuffles), four between the 16 warps of a CTA, eight between up to
+// 256 CTAs (in a final one-CTA kernel).
+//
+// Multiplication by a fixed element M is linear, so it is one table lookup per 4-bit nibble
+// of the other operand: Y * M = XOR over the 32 nibbles j of T_j[nibble_j(Y)], with
+// T_j[v] = (v placed at nibble j) * M; a table is 32 x 16 entries of 16 bytes (8 KiB).  The
+// per-block multiplier Q sits in shared memory beside the AES T-tables, replicated 8 times
+// so that lane l reads copy (l mod 8), which occupies its own four banks: every 16-byte
+// lookup of a warp is exactly four conflict-free shared-memory wavefronts, whatever the
+// data.  The tree's multipliers H^(2^j) use unreplicated tables.
+//
+// Three launches on the caller's stream: set-up (one CTA: H, Cipher(J0), H^(2^j) by
+// repeated squaring, all tables, into the caller's workspace), the data pass (persistent,
+// one CTA per SM: counter-mode AES with the T-table round code, a GHASH Horner step per
+// block, the in-CTA tree), and the final combine and tag.
+#include <cstring>
+
+#include "aes_ttable.cuh"
+
+namespace aesgb {
+namespace {
+
+using namespace tt;
+
+// ---- workspace layout (bytes) ------------------------------------------------------------
+constexpr size_t kQTab = 0;                           // Q table, 8 copies: 64 KiB
+constexpr size_t kPowTab = 65536;                     // tables of H^(2^j), j = 0..16
+constexpr int kPowTables = 17;
+constexpr size_t kVals = kPowTab + kPowTables * 8192;  // H, Cipher(J0)
+constexpr size_t kParts = kVals + 256;                // one partial sum per CTA
+constexpr int kMaxCtas = 256;
+constexpr size_t kWorkBytes = kParts + kMaxCtas * 16;
+constexpr int kThreads = 512;
+constexpr uint32_t kAesSmem = 2 * kRegion;            // encryption T-tables (128 KiB)
+constexpr uint32_t kMainSmem = kAesSmem + 65536;      // + replicated Q table
+
+// Element as four big-endian words, w0 the most significant (bytes 0..3): the view in which
+// multiplying by x is a right shift.
+struct Be {
+  uint32_t w0, w1, w2, w3;
+};
+
+__device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0u, 0x0123u); }
+__device__ __forceinline__ Be to_be(uint4 v) { return {bswap32(v.x), bswap32(v.y), bswap32(v.z), bswap32(v.w)}; }
+__device__ __forceinline__ uint4 to_le(Be b) { return make_uint4(bswap32(b.w0), bswap32(b.w1), bswap32(b.w2), bswap32(b.w3)); }
+__device__ __forceinline__ Be bxor(Be a, Be b) { return {a.w0 ^ b.w0, a.w1 ^ b.w1, a.w2 ^ b.w2, a.w3 ^ b.w3}; }
+__device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
+
+// b * x^r for 1 <= r <= 31: shift right by r; the r coefficients pushed past x^127 come back
+// as O * (1 + x + x^2 + x^7), O being those bits at the top (x^0 ..) of the element.
+__device__ __forceinline__ Be mulx_small(Be b, int r) {
+  const uint32_t out = b.w3 << (32 - r);
+  Be o{b.w0 >> r, __funnelshift_r(b.w1, b.w0, r), __funnelshift_r(b.w2, b.w1, r), __funnelshift_r(b.w3, b.w2, r)};
+  uint64_t t = uint64_t(out) << 32;
+  t ^= (t >> 1) ^ (t >> 2) ^ (t >> 7);
+  o.w0 ^= uint32_t(t >> 32);
+  o.w1 ^= uint32_t(t);
+  return o;
+}
+
+__device__ Be mulx(Be b, int k) {  // b * x^k, 0 <= k < 128
+  for (; k > 31; k -= 31) b = mulx_small(b, 31);
+  return k ? mulx_small(b, k) : b;
+}
+
+// Bit u of a 32-bit word to bit 2u of a 64-bit word.
+__device__ __forceinline__ uint64_t spread(uint32_t w) {
+  uint64_t x = w;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+// a^2 = sum a_i x^(2i): the bits spread apart give x^0..x^127 (upper half) and x^128..x^255
+// (lower half, B); then x^128 = 1 + x + x^2 + x^7 folds B back.
+__device__ Be square(Be a) {
+  const uint64_t r0 = spread(a.w0) << 1, r1 = spread(a.w1) << 1, r2 = spread(a.w2) << 1, r3 = spread(a.w3) << 1;
+  const Be lo{uint32_t(r0 >> 32), uint32_t(r0), uint32_t(r1 >> 32), uint32_t(r1)};
+  const Be b{uint32_t(r2 >> 32), uint32_t(r2), uint32_t(r3 >> 32), uint32_t(r3)};
+  return bxor(bxor(lo, b), bxor(mulx_small(b, 1), bxor(mulx_small(b, 2), mulx_small(b, 7))));
+}
+
+// Entry v of nibble table j for multiplier m: sum over the bits of v of m * x^(4j + b),
+// bit 3 of v standing for x^(4j).
+__device__ uint4 table_entry(Be m, int j, int v) {
+  Be base = mulx(m, 4 * j), acc{0, 0, 0, 0};
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    if ((v >> (3 - b)) & 1) acc = bxor(acc, base);
+    base = mulx_small(base, 1);
+  }
+  return to_le(acc);
+}
+
+// y * M with M's unreplicated table (512 entries, entry j*16 + v).
+__device__ __forceinline__ uint4 mul_tab(uint4 y, const uint4* tab) {
+  uint4 acc = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t w = j < 8 ? y.x : j < 16 ? y.y : j < 24 ? y.z : y.w;
+    const uint32_t s = 8u * ((j >> 1) & 3) + ((j & 1) ? 0u : 4u);
+    acc = xor4(acc, tab[j * 16 + ((w >> s) & 15u)]);
+  }
+  return acc;
+}
+
+// y * Q with the replicated table: entry (j, v) of copy c at j*2048 + v*128 + c*16, and qb
+// already points at copy (lane mod 8).  The byte offset of v is one shift and one AND.
+__device__ __forceinline__ uint4 mul_q(uint4 y, const char* qb) {
+  uint4 acc = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t w = j < 8 ? y.x : j < 16 ? y.y : j < 24 ? y.z : y.w;
+    const int s = 8 * ((j >> 1) & 3) + ((j & 1) ? 0 : 4);
+    const uint32_t off = s >= 7 ? (w >> (s - 7)) & 0x780u : (w << (7 - s)) & 0x780u;
+    acc = xor4(acc, *reinterpret_cast<const uint4*>(qb + j * 2048 + off));
+  }
+  return acc;
+}
+
+__device__ __forceinline__ uint4 shfl_down4(uint4 v, int d) {
+  return make_uint4(__shfl_down_sync(0xFFFFFFFFu, v.x, d), __shfl_down_sync(0xFFFFFFFFu, v.y, d),
+                    __shfl_down_sync(0xFFFFFFFFu, v.z, d), __shfl_down_sync(0xFFFFFFFFu, v.w, d));
+}
+
+// Binary tree over the lanes of a warp, `levels` levels: level j pairs lane i (a multiple of
+// 2^(j+1)) with lane i + 2^j as v_i * M_j + v_(i + 2^j), M_j the multiplier of table tabs[j].
+// With M_j = M^(2^j), lane 0 ends with sum_l v_l M^(2^levels - 1 - l).
+__device__ __forceinline__ uint4 lane_tree(uint4 v, const uint4* tabs, int levels) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (int j = 0; j < levels; ++j) {
+    const uint4 o = shfl_down4(v, 1 << j);
+    const uint4 m = mul_tab(v, tabs + j * 512);
+    if ((lane & ((2u << j) - 1u)) == 0) v = xor4(m, o);
+  }
+  return v;
+}
+
+// Up to 16 bytes from p (the rest zero); never reads past p[nb - 1].
+__device__ __forceinline__ uint4 ld_partial(const uint8_t* p, uint32_t nb) {
+  uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int b = 0; b < 16; ++b)
+    if (uint32_t(b) < nb) w[b >> 2] |= uint32_t(p[b]) << (8 * (b & 3));
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ void st_partial(uint8_t* p, uint4 v, uint32_t nb) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int b = 0; b < 16; ++b)
+    if (uint32_t(b) < nb) p[b] = uint8_t(w[b >> 2] >> (8 * (b & 3)));
+}
+
+__device__ __forceinline__ uint32_t byte_mask(uint32_t nb, int q) {  // bytes 4q.. of the first nb
+  const int n = int(nb) - 4 * q;
+  return n >= 4 ? 0xFFFFFFFFu : n <= 0 ? 0u : (1u << (8 * n)) - 1u;
+}
+
+struct GcmArgs {
+  const uint4* in;
+  uint4* out;
+  const uint8_t* aad;
+  uint64_t z;        // leading zero positions
+  uint64_t a;        // AAD blocks
+  uint64_t aad_len;  // bytes
+  uint64_t len;      // data bytes
+  uint32_t K;        // positions per thread
+  uint32_t iv0, iv1, iv2;
+  int decrypt;
+};
+
+// ---- set-up: H, Cipher(J0), powers, tables ------------------------------------------------
+template <int NR>
+__global__ void __launch_bounds__(kThreads, 1)
+gcm_setup(const KeyWords kw, uint32_t iv0, uint32_t iv1, uint32_t iv2, uint32_t T, char* work) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint4 s_he[2];
+  __shared__ Be s_pow[18];
+  __shared__ Be s_q;
+  fill_tables<AES_ENCRYPT>(smem);
+  __syncthreads();
+  const uint32_t tid = threadIdx.x;
+  if (tid < 2) {
+    const uint4 v = tid ? make_uint4(iv0, iv1, iv2, bswap32(1u)) : make_uint4(0, 0, 0, 0);
+    s_he[tid] = crypt_block<NR, AES_ENCRYPT>(v, kw, reinterpret_cast<const char*>(smem), (tid & 31u) * 4u);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    Be p = to_be(s_he[0]);
+    s_pow[0] = p;
+    for (int j = 1; j < 18; ++j) s_pow[j] = p = square(p);
+  }
+  __syncthreads();
+  uint4* pow_tab = reinterpret_cast<uint4*>(work + kPowTab);
+  const int j = int(tid >> 4), v = int(tid & 15u);
+  for (int m = 0; m < kPowTables; ++m) pow_tab[m * 512 + tid] = table_entry(s_pow[m], j, v);
+  __syncthreads();  // the tables are read back below (block-wide visibility of global writes)
+  if (tid == 0) {
+    int hi = 31 - __clz(T);  // T < 2^18
+    uint4 q = to_le(s_pow[hi]);
+    for (int b = 0; b < hi; ++b)
+      if ((T >> b) & 1u) q = mul_tab(q, pow_tab + b * 512);
+    s_q = to_be(q);
+  }
+  __syncthreads();
+  const uint4 e = table_entry(s_q, j, v);
+  uint4* qtab = reinterpret_cast<uint4*>(work + kQTab);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) qtab[tid * 8 + c] = e;
+  if (tid < 2) reinterpret_cast<uint4*>(work + kVals)[tid] = s_he[tid];
+}
+
+// ---- data pass ------------------------------------------------------------------------------
+template <int NR, int U>
+__global__ void __launch_bounds__(kThreads, 1)
+gcm_main(const GcmArgs g, const KeyWords kw, char* work) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint4 s_warp[kThreads / 32];
+  fill_tables<AES_ENCRYPT>(smem);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(work + kQTab);
+    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(smem) + kAesSmem);
+    for (uint32_t i = threadIdx.x; i < 65536 / 16; i += kThreads) dst[i] = src[i];
+  }
+  __syncthreads();
+  const char* sm = reinterpret_cast<const char*>(smem);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lc = lane * 4u;
+  const char* qb = sm + kAesSmem + (lane & 7u) * 16u;
+  const uint64_t T = uint64_t(gridDim.x) * kThreads;
+  const uint64_t t = uint64_t(blockIdx.x) * kThreads + threadIdx.x;
+  const uint64_t cblocks = (g.len + 15) / 16;
+
+  uint4 y = make_uint4(0, 0, 0, 0);
+  for (uint32_t k = 0; k < g.K; k += U) {
+    uint4 x[U], ctr[U];
+    int kind[U];  // 0 nothing, 1 AAD block, 2 data block
+    uint64_t idx[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t p = t + uint64_t(k + u) * T;
+      kind[u] = 0;
+      idx[u] = 0;
+      x[u] = make_uint4(0, 0, 0, 0);
+      if (k + u < g.K && p >= g.z) {
+        const uint64_t i = p - g.z;
+        if (i < g.a) {
+          kind[u] = 1;
+          idx[u] = i;
+          x[u] = 16 * (i + 1) <= g.aad_len ? ld_block(reinterpret_cast<const uint4*>(g.aad) + i)
+                                           : ld_partial(g.aad + 16 * i, uint32_t(g.aad_len - 16 * i));
+        } else if (i - g.a < cblocks) {
+          const uint64_t jb = i - g.a;
+          kind[u] = 2;
+          idx[u] = jb;
+          x[u] = 16 * (jb + 1) <= g.len ? ld_block(g.in + jb)
+                                        : ld_partial(reinterpret_cast<const uint8_t*>(g.in) + 16 * jb, uint32_t(g.len - 16 * jb));
+        }
+      }
+      ctr[u] = make_uint4(g.iv0, g.iv1, g.iv2, bswap32(uint32_t(2u + uint32_t(idx[u]))));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) ctr[u] = crypt_block<NR, AES_ENCRYPT>(ctr[u], kw, sm, lc);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      uint4 h = x[u];
+      if (kind[u] == 2) {
+        const uint64_t jb = idx[u];
+        const uint4 o = xor4(x[u], ctr[u]);
+        if (16 * (jb + 1) <= g.len) {
+          st_block(g.out + jb, o);
+          if (!g.decrypt) h = o;
+        } else {
+          const uint32_t nb = uint32_t(g.len - 16 * jb);
+          st_partial(reinterpret_cast<uint8_t*>(g.out) + 16 * jb, o, nb);
+          if (!g.decrypt)
+            h = make_uint4(o.x & byte_mask(nb, 0), o.y & byte_mask(nb, 1), o.z & byte_mask(nb, 2), o.w & byte_mask(nb, 3));
+        }
+      }
+      if (k + u < g.K) y = xor4(mul_q(y, qb), h);
+    }
+  }
+
+  // In-CTA tree: sum_i Y_i H^(511 - i) over the CTA's threads.
+  __syncthreads();  // the AES and Q tables are no longer needed
+  uint4* tabs = reinterpret_cast<uint4*>(smem);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(work + kPowTab);
+    for (uint32_t i = threadIdx.x; i < 9 * 512; i += kThreads) tabs[i] = src[i];
+  }
+  __syncthreads();
+  y = lane_tree(y, tabs, 5);
+  if (lane == 0) s_warp[threadIdx.x >> 5] = y;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint4 w = lane < kThreads / 32 ? s_warp[lane] : make_uint4(0, 0, 0, 0);
+    w = lane_tree(w, tabs + 5 * 512, 4);
+    if (lane == 0) reinterpret_cast<uint4*>(work + kParts)[blockIdx.x] = w;
+  }
+}
+
+// ---- combine and tag -------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 1)
+gcm_final(const char* work, uint32_t nb, uint64_t abits, uint64_t cbits, uint8_t* tag) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint4 s_warp[8];
+  uint4* tabs = reinterpret_cast<uint4*>(smem);  // H^(2^9) .. H^(2^16), then H
+  const uint4* pow_tab = reinterpret_cast<const uint4*>(work + kPowTab);
+  for (uint32_t i = threadIdx.x; i < 8 * 512; i += 256) tabs[i] = pow_tab[9 * 512 + i];
+  for (uint32_t i = threadIdx.x; i < 512; i += 256) tabs[8 * 512 + i] = pow_tab[i];
+  __syncthreads();
+  // CTA b sits at slot 256 - nb + b, so slot s carries the power (H^512)^(255 - s).
+  const uint32_t s = threadIdx.x, lane = s & 31u;
+  const uint4* parts = reinterpret_cast<const uint4*>(work + kParts);
+  uint4 v = s >= kMaxCtas - nb ? parts[s - (kMaxCtas - nb)] : make_uint4(0, 0, 0, 0);
+  v = lane_tree(v, tabs, 5);
+  if (lane == 0) s_warp[s >> 5] = v;
+  __syncthreads();
+  if (s < 32) {
+    uint4 w = lane < 8 ? s_warp[lane] : make_uint4(0, 0, 0, 0);
+    w = lane_tree(w, tabs + 5 * 512, 3);
+    if (lane == 0) {
+      const uint4* h_tab = tabs + 8 * 512;
+      const uint4 gsum = mul_tab(w, h_tab);  // sum_i X_i H^(n - i)
+      const uint4 L = make_uint4(bswap32(uint32_t(abits >> 32)), bswap32(uint32_t(abits)), bswap32(uint32_t(cbits >> 32)),
+                                 bswap32(uint32_t(cbits)));
+      const uint4 S = mul_tab(xor4(gsum, L), h_tab);
+      const uint4 ej0 = reinterpret_cast<const uint4*>(work + kVals)[1];
+      const uint4 t = xor4(ej0, S);
+      const uint32_t tw[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int b = 0; b < 16; ++b) tag[b] = uint8_t(tw[b >> 2] >> (8 * (b & 3)));
+    }
+  }
+}
+
+constexpr int kUnroll = 2;
+using SetupFn = void (*)(const KeyWords, uint32_t, uint32_t, uint32_t, uint32_t, char*);
+using MainFn = void (*)(const GcmArgs, const KeyWords, char*);
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return na && nb && x < y + nb && y < x + na;
+}
+
+}  // namespace
+}  // namespace aesgb
+
+using namespace aesgb;
+
+extern "C" size_t aes_gcm_workspace_bytes(void) { return kWorkBytes; }
+
+extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* iv, size_t iv_len, const void* d_aad,
+                                    size_t aad_len, const void* d_in, void* d_out, size_t nbytes, int dir, uint8_t* d_tag,
+                                    void* d_work, size_t work_bytes, void* cuda_stream) {
+  clear_error();
+  if (!schedule_ok(ks)) return set_error(AES_EINVAL, "invalid key schedule (nr must be 10, 12 or 14)");
+  if (dir != AES_ENCRYPT && dir != AES_DECRYPT) return set_error(AES_EINVAL, "dir must be AES_ENCRYPT or AES_DECRYPT");
+  if (!iv || iv_len != 12) return set_error(AES_EINVAL, "GCM takes a 12-byte (96-bit) IV");
+  if (!d_tag) return set_error(AES_EINVAL, "null tag");
+  if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & 15u) || work_bytes < kWorkBytes)
+    return set_error(AES_EINVAL, "workspace must be 16-byte aligned and at least %zu bytes", kWorkBytes);
+  if (nbytes > (size_t(0xFFFFFFFFu) - 1u) * 16u)
+    return set_error(AES_EINVAL, "GCM data is limited to 2^32 - 2 blocks");
+  if (aad_len > (size_t(1) << 36)) return set_error(AES_EINVAL, "AAD is limited to 64 GiB");
+  if (nbytes && (!d_in || !d_out)) return set_error(AES_EINVAL, "null buffer");
+  if (aad_len && !d_aad) return set_error(AES_EINVAL, "null AAD");
+  if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out) | reinterpret_cast<uintptr_t>(d_aad)) & 15u))
+    return set_error(AES_EINVAL, "data and AAD buffers must be 16-byte aligned");
+  if (d_in != d_out && overlaps(d_in, nbytes, d_out, nbytes))
+    return set_error(AES_EINVAL, "input and output overlap without being identical");
+  if (overlaps(d_out, nbytes, d_aad, aad_len)) return set_error(AES_EINVAL, "output overlaps the AAD");
+  if (overlaps(d_work, kWorkBytes, d_in, nbytes) || overlaps(d_work, kWorkBytes, d_out, nbytes) ||
+      overlaps(d_work, kWorkBytes, d_aad, aad_len) || overlaps(d_work, kWorkBytes, d_tag, 16))
+    return set_error(AES_EINVAL, "workspace overlaps a buffer");
+  const DeviceInfo* di = current_device_info();
+  if (!di) return AES_ECUDA;
+  if (di->smem_optin < int(kMainSmem)) return set_error(AES_EINVAL, "device has too little shared memory for GCM");
+
+  const uint64_t a = (aad_len + 15) / 16, c = (nbytes + 15) / 16, n = a + c;
+  const int max_ctas = di->sms < kMaxCtas ? di->sms : kMaxCtas;
+  uint64_t want = (n + uint64_t(kThreads) * 4 - 1) / (uint64_t(kThreads) * 4);
+  const uint32_t nb = n == 0 ? 0u : uint32_t(want < 1 ? 1 : want > uint64_t(max_ctas) ? uint64_t(max_ctas) : want);
+  const uint32_t T = (nb ? nb : 1u) * kThreads;
+  uint32_t ivw[3];
+  std::memcpy(ivw, iv, 12);
+  const KeyWords kw = enc_key_words(*ks, nullptr);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  char* work = static_cast<char*>(d_work);
+
+  SetupFn setup = ks->nr == 10 ? gcm_setup<10> : ks->nr == 12 ? gcm_setup<12> : gcm_setup<14>;
+  MainFn main_k = ks->nr == 10 ? gcm_main<10, kUnroll> : ks->nr == 12 ? gcm_main<12, kUnroll> : gcm_main<14, kUnroll>;
+  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(setup), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kAesSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(main_k), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMainSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(gcm_final), cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 8192);
+  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(GCM)");
+
+  setup<<<1, kThreads, kAesSmem, st>>>(kw, ivw[0], ivw[1], ivw[2], T, work);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM set-up launch");
+  if (nb) {
+    GcmArgs g;
+    g.in = static_cast<const uint4*>(d_in);
+    g.out = static_cast<uint4*>(d_out);
+    g.aad = static_cast<const uint8_t*>(d_aad);
+    g.K = uint32_t((n + T - 1) / T);
+    g.z = uint64_t(g.K) * T - n;
+    g.a = a;
+    g.aad_len = aad_len;
+    g.len = nbytes;
+    g.iv0 = ivw[0];
+    g.iv1 = ivw[1];
+    g.iv2 = ivw[2];
+    g.decrypt = dir == AES_DECRYPT;
+    main_k<<<nb, kThreads, kMainSmem, st>>>(g, kw, work);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM data-pass launch");
+  }
+  gcm_final<<<1, 256, 9 * 8192, st>>>(work, nb, uint64_t(aad_len) * 8u, uint64_t(nbytes) * 8u, d_tag);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM final launch");
+  return AES_OK;
+}

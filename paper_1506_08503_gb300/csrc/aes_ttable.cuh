@@ -59,18 +59,22 @@ __device__ __forceinline__ uint32_t pick_bytes(uint32_t a, uint32_t b, uint32_t 
 template <int DIR>
 __device__ __forceinline__ void fill_tables(uint32_t* sm) {
   // Regions 0 and 1: T0|T1 and T2|T3 (rotations of Te0 or Td0).  Region 2 (decryption
-  // only): InvS replicated into all four bytes, for the last round.
-  constexpr int kWords = (DIR == AES_ENCRYPT) ? 2 * 16384 : 3 * 16384;
-  for (int w = threadIdx.x; w < kWords; w += blockDim.x) {
+  // only): InvS replicated into all four bytes, for the last round.  The 256-entry base
+  // tables are staged once (one global read each), then every 16-byte store writes four
+  // lanes' copies of one entry.
+  __shared__ uint32_t stage[DIR == AES_ENCRYPT ? 256 : 512];
+  for (int x = threadIdx.x; x < 256; x += blockDim.x) {
+    stage[x] = (DIR == AES_ENCRYPT) ? g_field_tables.te0[x] : g_field_tables.td0[x];
+    if (DIR != AES_ENCRYPT) stage[256 + x] = g_field_tables.is4[x];
+  }
+  __syncthreads();
+  constexpr int kVecs = ((DIR == AES_ENCRYPT) ? 2 : 3) * 16384 / 4;
+  uint4* sm4 = reinterpret_cast<uint4*>(sm);
+  for (int q = threadIdx.x; q < kVecs; q += blockDim.x) {
+    const int w = 4 * q;  // first of the four words (lanes 4q..4q+3 of one entry)
     const int region = w >> 14, x = (w >> 6) & 255, half = (w >> 5) & 1;
-    uint32_t v;
-    if (region < 2) {
-      const uint32_t base = (DIR == AES_ENCRYPT) ? g_field_tables.te0[x] : g_field_tables.td0[x];
-      v = rotl32(base, 8 * (2 * region + half));
-    } else {
-      v = half ? 0u : g_field_tables.is4[x];
-    }
-    sm[w] = v;
+    const uint32_t v = region < 2 ? rotl32(stage[x], 8 * (2 * region + half)) : (half ? 0u : stage[256 + x]);
+    sm4[q] = make_uint4(v, v, v, v);
   }
 }
 

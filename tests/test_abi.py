@@ -108,3 +108,31 @@ def test_pool_and_batch_null_handling_without_gpu(aes):
 def test_message_struct_layout(aes):
     assert ctypes.sizeof(aes.aes_msg) == 24 == aes.msg_dtype().itemsize
     assert ctypes.sizeof(aes.aes_key_schedule) == 4 + 15 * 16
+
+
+def test_gcm_argument_checks_before_any_cuda_call(aes):
+    lib = aes.lib()
+    ks = aes.aes_key_expand(bytes(16))
+    kp = ctypes.byref(ks)
+    iv = (ctypes.c_uint8 * 16)()
+    base = 1 << 40  # never dereferenced
+    W = aes.aes_gcm_workspace_bytes()
+    assert W >= 64 * 1024
+    work, tag = base + (1 << 30), base + (1 << 31)
+
+    def call(iv_len=12, aad=None, aad_len=0, src=base, dst=base, n=64, d=0, t=tag, w=work, wb=W):
+        return lib.aes_gcm_crypt(kp, iv, iv_len, aad, aad_len, src, dst, n, d, t, w, wb, None)
+
+    for iv_len in (0, 8, 16):
+        assert call(iv_len=iv_len) == aes.AES_EINVAL and "IV" in aes.aes_last_error()
+    assert call(wb=W - 16) == aes.AES_EINVAL  # workspace too small
+    assert call(w=work + 8) == aes.AES_EINVAL  # workspace misaligned
+    assert call(w=base + 32) == aes.AES_EINVAL  # workspace overlaps the data
+    assert call(t=None) == aes.AES_EINVAL
+    assert call(d=3) == aes.AES_EINVAL
+    assert call(src=base + 8) == aes.AES_EINVAL  # misaligned data
+    assert call(dst=base + 16) == aes.AES_EINVAL  # partial overlap
+    assert call(aad=None, aad_len=5) == aes.AES_EINVAL
+    assert call(aad=base + 48, aad_len=32) == aes.AES_EINVAL  # output overlaps the AAD
+    assert call(n=16 * (1 << 32)) == aes.AES_EINVAL  # beyond 2^32 - 2 blocks
+    assert call(src=None, dst=None) == aes.AES_EINVAL

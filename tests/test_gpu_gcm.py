@@ -1,0 +1,130 @@
+"""GPU parity for AES-GCM (the counter-based authenticated mode that Section V of the paper
+names as future work; NIST SP 800-38D with 96-bit IVs) against the oracle's GCM.
+
+Output bytes and tags are compared exactly.  Sizes span one to many CTAs, several positions
+per thread, ragged final blocks of data and AAD, and the empty cases.  At 1 GiB the
+ciphertext is checked on sampled blocks against the oracle's cipher of the counter blocks,
+decryption must return the plaintext and the same tag, and the tag of a sparse ciphertext is
+compared with its closed form sum_j C_j H^(c - j + 1) + L H + Cipher(J0), evaluated with the
+oracle's GF(2^128) product.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    import torch
+
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+CASES = [(0, 0), (0, 13), (1, 0), (16, 16), (15, 17), (4095, 33), (16 * 2048 + 5, 100),
+         (16 * 77_824 + 9, 0), (16 * (3 * 77_824 + 1000) + 3, 4100)]
+
+
+@pytest.mark.parametrize("key_bits", [128, 192, 256])
+@pytest.mark.parametrize("nbytes,aad_len", CASES)
+def test_gcm_matches_oracle(aes, orc, cuda, key_bits, nbytes, aad_len):
+    if key_bits != 128 and nbytes > 16 * 100_000:
+        pytest.skip("large sizes run with AES-128 only")
+    rng = np.random.default_rng(nbytes * 7 + aad_len + key_bits)
+    key = rng.integers(0, 256, key_bits // 8, dtype=np.uint8)
+    iv = rng.integers(0, 256, 12, dtype=np.uint8)
+    pt = rng.integers(0, 256, nbytes, dtype=np.uint8)
+    aad = rng.integers(0, 256, aad_len, dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes(), key_bits)
+    want_ct, want_tag = orc.gcm_crypt(key, iv, pt, aad)
+    ct, tag = aes.gcm(dev(pt), ks, iv.tobytes(), aad=dev(aad) if aad_len else None)
+    assert (host(ct) == want_ct).all()
+    assert (host(tag) == want_tag).all()
+    back, tag2 = aes.gcm(ct, ks, iv.tobytes(), aad=dev(aad) if aad_len else None, dir="decrypt")
+    assert (host(back) == pt).all() and (host(tag2) == want_tag).all()
+
+
+def test_gcm_decrypt_of_arbitrary_data_and_in_place(aes, orc, cuda):
+    rng = np.random.default_rng(9)
+    key, iv = rng.integers(0, 256, 32, dtype=np.uint8), rng.integers(0, 256, 12, dtype=np.uint8)
+    data, aad = rng.integers(0, 256, 16 * 50_001 + 7, dtype=np.uint8), rng.integers(0, 256, 40, dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes(), 256)
+    want, want_tag = orc.gcm_crypt(key, iv, data, aad, decrypt=True)
+    x = dev(data)
+    _, tag = aes.gcm(x, ks, iv.tobytes(), aad=dev(aad), dir="decrypt", out=x)
+    assert (host(x) == want).all() and (host(tag) == want_tag).all()
+
+
+def test_gcm_calls_in_a_row_share_nothing(aes, orc, cuda):
+    # different keys, IVs and sizes back to back on one stream, each with a fresh workspace
+    rng = np.random.default_rng(10)
+    outs = []
+    for n in (5000, 16, 16 * 300_000):
+        key, iv = rng.integers(0, 256, 16, dtype=np.uint8), rng.integers(0, 256, 12, dtype=np.uint8)
+        pt = rng.integers(0, 256, n, dtype=np.uint8)
+        ct, tag = aes.gcm(dev(pt), aes.aes_key_expand(key.tobytes()), iv.tobytes())
+        outs.append((key, iv, pt, ct, tag))
+    for key, iv, pt, ct, tag in outs:
+        want_ct, want_tag = orc.gcm_crypt(key, iv, pt)
+        assert (host(ct) == want_ct).all() and (host(tag) == want_tag).all()
+
+
+def _power(orc, h, e):
+    acc = np.array([0x80] + [0] * 15, dtype=np.uint8)
+    sq = h.copy()
+    while e:
+        if e & 1:
+            acc = orc.gf128_mul(acc, sq)
+        sq = orc.gf128_mul(sq, sq)
+        e >>= 1
+    return acc
+
+
+def test_gcm_full_size_1gib(aes, orc, cuda):
+    """2^26 blocks (1 GiB): the bench's GCM workload and launch."""
+    import torch
+
+    c = 1 << 26
+    rng = np.random.default_rng(11)
+    key, iv = rng.integers(0, 256, 16, dtype=np.uint8), rng.integers(0, 256, 12, dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes())
+    g = torch.Generator(device="cuda").manual_seed(11)
+    x = torch.randint(0, 256, (16 * c,), dtype=torch.uint8, device="cuda", generator=g)
+    ct, tag = aes.gcm(x, ks, iv.tobytes())
+    # sampled blocks: C_j = P_j + Cipher(IV || 2 + j)
+    idx = np.unique(np.concatenate([[0, 1, c // 2, c - 2, c - 1], rng.integers(0, c, 2000)]))
+    ti = torch.from_numpy(idx).cuda()
+    p = x.view(-1, 16)[ti].cpu().numpy()
+    got = ct.view(-1, 16)[ti].cpu().numpy()
+    ctrs = np.zeros((idx.size, 16), dtype=np.uint8)
+    ctrs[:, :12] = iv
+    ctrs[:, 12:] = np.frombuffer(b"".join(int(2 + j).to_bytes(4, "big") for j in idx), dtype=np.uint8).reshape(-1, 4)
+    ks_blocks = orc.encrypt_blocks(key, ctrs.reshape(-1), threads=8).reshape(-1, 16)
+    assert (got == (p ^ ks_blocks)).all()
+    # decryption returns the plaintext and the same tag
+    back, tag2 = aes.gcm(ct, ks, iv.tobytes(), dir="decrypt")
+    torch.cuda.synchronize()
+    assert torch.equal(back, x) and torch.equal(tag, tag2)
+    del back, ct
+    # sparse ciphertext: the tag has a closed form in H
+    h = orc.encrypt_blocks(key, np.zeros(16, dtype=np.uint8))
+    ej0 = orc.encrypt_blocks(key, np.concatenate([iv, np.array([0, 0, 0, 1], dtype=np.uint8)]))
+    x.zero_()
+    pos = [0, 1, 77_823, 77_824, c // 3, c - 2, c - 1]
+    vals = rng.integers(0, 256, (len(pos), 16), dtype=np.uint8)
+    x.view(-1, 16)[torch.tensor(pos, device="cuda")] = torch.from_numpy(vals).cuda()
+    _, tag3 = aes.gcm(x, ks, iv.tobytes(), dir="decrypt")
+    s = np.zeros(16, dtype=np.uint8)
+    for j, v in zip(pos, vals):
+        s ^= orc.gf128_mul(v, _power(orc, h, c - j + 1))
+    lens = np.frombuffer((0).to_bytes(8, "big") + (128 * c).to_bytes(8, "big"), dtype=np.uint8)
+    s ^= orc.gf128_mul(lens, h)
+    assert (host(tag3) == (ej0 ^ s)).all()
+    del x
+    torch.cuda.empty_cache()
