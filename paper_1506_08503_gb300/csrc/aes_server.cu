@@ -12,15 +12,23 @@
 // Requests arriving while batches run are admitted into the next free stream's batch, so the
 // device works on several batches at once and nobody waits for a full drain.
 //
+// Threads: the worker only admits (under the server mutex); each stream slot has an issuer
+// thread that builds the admitted batch's descriptors and launches it, so the host work of
+// several batches (linear in their request counts) proceeds in parallel.  A bulk submission
+// reserves all its tickets at once and writes them in chunks, so admission starts before the
+// whole submission is written.
+//
 // Staging memory is one cudaMalloc'd arena (the HBM budget) managed by a first-fit free list
 // with coalescing; a request is admitted only when its staging fits (head-of-line order is
 // kept, so large requests are not starved by small ones).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -73,7 +81,6 @@ class Arena {
     }
     free_[off] = bytes;
   }
-  size_t largest_possible() const { return size_; }
 
  private:
   std::map<size_t, size_t> free_;
@@ -81,21 +88,27 @@ class Arena {
 };
 
 // One request slot of the ring.  Ticket t lives in ring[t & mask] from submission until a
-// poll reports it finished; ticket == 0 marks a free slot.
+// poll releases it.  `ticket` (0 = free) is stored last, with release order, once the request
+// is in place; `state` moves PENDING -> DONE or FAILED once.  Both are atomic because the
+// thread that owns a reserved or in-flight ticket range writes them without the server mutex.
 struct Req {
   aes_request r{};
-  uint64_t ticket = 0;
   double t_submit = 0;
-  int state = AES_REQ_PENDING;
-  bool staged = false;
   size_t stage_off = 0, stage_bytes = 0;
+  bool staged = false;
+  std::atomic<int> state{AES_REQ_PENDING};
+  std::atomic<uint64_t> ticket{0};
 };
 
 struct StreamSlot {
   cudaStream_t stream = nullptr;
   aes_batch* batch = nullptr;
-  bool busy = false;
+  bool busy = false;         // admitted and not yet retired
+  bool pending = false;      // admitted, waiting for this slot's issuer thread
+  bool inject_fail = false;  // fault injection: the issuer fails this batch
   uint64_t first = 0, last = 0;  // the batch is the ticket range [first, last)
+  std::vector<double> lat;   // retirement scratch (max_batch entries)
+  std::vector<std::pair<size_t, size_t>> frees;
 };
 
 struct DoneMsg {
@@ -118,14 +131,19 @@ struct aes_server {
   std::vector<DoneMsg> done_msgs;
 
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::vector<Req> ring;       // power-of-two size >= queue_capacity
+  std::condition_variable cv_work, cv_done, cv_issue;
+  std::unique_ptr<Req[]> ring;  // power-of-two size >= queue_capacity
+  uint64_t ring_size = 0;
   uint64_t mask = 0;
-  uint64_t next_ticket = 1;    // next ticket to hand out
-  uint64_t admit = 1;          // first ticket not admitted yet: the queue is [admit, next_ticket)
+  uint64_t next_ticket = 1;    // next ticket to hand out (tickets below it are reserved)
+  uint64_t filled = 1;         // first ticket whose request is not yet in the ring
+  uint64_t oldest = 1;         // first ticket not yet released by a poll
+  uint64_t admit = 1;          // first ticket not admitted yet: the queue is [admit, filled)
   uint64_t inflight = 0;
   bool stop = false;
+  bool stop_issuers = false;
   std::thread worker;
+  std::vector<std::thread> issuers;  // one per stream slot
 
   // statistics
   std::vector<double> lat_us;
@@ -137,41 +155,48 @@ struct aes_server {
 
 namespace {
 
-// Forward declaration: the callback retires its batch itself.
-void retire(aes_server* s, StreamSlot& sl, double t, int state);
-
-// Runs on a CUDA driver thread once everything queued for the batch has finished (no CUDA
-// calls here): marks the batch's requests done, frees their staging and wakes everyone.
-void CUDART_CB on_batch_done(void* p) {
-  DoneMsg* m = static_cast<DoneMsg*>(p);
-  aes_server* s = m->s;
-  const double t = now_s();
+// Finishes a slot's batch: every request's state becomes `state` (DONE or FAILED), then the
+// counters, latencies and staging frees are applied under the mutex in one step.  The slot's
+// ticket range belongs to the batch until its states are stored, so the per-request pass
+// needs no lock; a request is not touched after its state store (a poll may then release and
+// reuse its slot).  Waiters are woken after the locked step, so no wake-up is lost.  Called
+// WITHOUT mu held.
+void retire(aes_server* s, StreamSlot& sl, double t, int state) {
+  sl.lat.clear();
+  sl.frees.clear();
+  uint64_t bytes = 0;
+  const uint64_t n = sl.last - sl.first;
+  for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
+    Req& q = s->at(tk);
+    if (q.staged) sl.frees.emplace_back(q.stage_off, q.stage_bytes);
+    q.staged = false;
+    bytes += q.r.length;
+    if (state == AES_REQ_DONE) sl.lat.push_back((t - q.t_submit) * 1e6);
+    q.state.store(state, std::memory_order_release);
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    retire(s, s->slots[m->slot], t, AES_REQ_DONE);
+    for (const auto& f : sl.frees) s->arena.release(f.first, f.second);
+    s->inflight -= n;
+    if (state == AES_REQ_DONE) {
+      s->completed += n;
+      s->bytes_done += bytes;
+      s->lat_us.insert(s->lat_us.end(), sl.lat.begin(), sl.lat.end());
+      if (t > s->t_last) s->t_last = t;
+    } else {
+      s->failed += n;
+    }
+    sl.busy = false;
   }
   s->cv_done.notify_all();
   s->cv_work.notify_one();
 }
 
-// Marks a slot's requests finished (state DONE or FAILED) and frees their staging.  Holds mu.
-void retire(aes_server* s, StreamSlot& sl, double t, int state) {
-  for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
-    Req& q = s->at(tk);
-    if (q.staged) s->arena.release(q.stage_off, q.stage_bytes);
-    q.staged = false;
-    q.state = state;
-    --s->inflight;
-    if (state == AES_REQ_DONE) {
-      ++s->completed;
-      s->bytes_done += q.r.length;
-      s->lat_us.push_back((t - q.t_submit) * 1e6);
-    } else {
-      ++s->failed;
-    }
-  }
-  if (state == AES_REQ_DONE && t > s->t_last) s->t_last = t;
-  sl.busy = false;
+// Runs on a CUDA driver thread once everything queued for the batch has finished (no CUDA
+// calls here).
+void CUDART_CB on_batch_done(void* p) {
+  DoneMsg* m = static_cast<DoneMsg*>(p);
+  retire(m->s, m->s->slots[m->slot], now_s(), AES_REQ_DONE);
 }
 
 // Issues the tickets [sl.first, sl.last) on slot i (mu NOT held; the batch owns its ring
@@ -180,8 +205,7 @@ aes_status issue(aes_server* s, int i) {
   StreamSlot& sl = s->slots[i];
   cudaStream_t st = sl.stream;
   cudaError_t e;
-  if (s->cfg.fail_every && s->launches % s->cfg.fail_every == 0)  // launches n, 2n, 3n, ...: fake a failure
-    return set_error(AES_ECUDA, "injected launch failure (fail_every = %u)", s->cfg.fail_every);
+  if (sl.inject_fail) return set_error(AES_ECUDA, "injected launch failure (fail_every = %u)", s->cfg.fail_every);
   // pass 1: host payloads go to the device, and the batch is counted per direction
   size_t nenc = 0, ndec = 0;
   for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
@@ -221,6 +245,29 @@ aes_status issue(aes_server* s, int i) {
   return AES_OK;
 }
 
+// One thread per stream slot builds and launches the slot's batches, so that the descriptor
+// work of several batches (linear in their request counts) runs in parallel while the worker
+// keeps admitting.
+void issuer_main(aes_server* s, int i) {
+  cudaSetDevice(s->device);
+  StreamSlot& sl = s->slots[i];
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    s->cv_issue.wait(lk, [&] { return sl.pending || s->stop_issuers; });
+    if (!sl.pending) break;
+    sl.pending = false;
+    lk.unlock();
+    const aes_status rc = issue(s, i);
+    if (rc != AES_OK) {
+      cudaStreamSynchronize(sl.stream);  // copies queued before the failure may still read the staging
+      retire(s, sl, now_s(), AES_REQ_FAILED);
+    }
+    lk.lock();
+  }
+}
+
+constexpr uint64_t kInlineIssue = 256;  // batches up to this many requests skip the hand-off
+
 void worker_main(aes_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
@@ -233,8 +280,8 @@ void worker_main(aes_server* s) {
     }
     if (s->stop) {
       // fail whatever is still queued, then wait for the GPU to finish what it has
-      for (; s->admit < s->next_ticket; ++s->admit) {
-        s->at(s->admit).state = AES_REQ_FAILED;
+      for (; s->admit < s->filled; ++s->admit) {
+        s->at(s->admit).state.store(AES_REQ_FAILED, std::memory_order_release);
         ++s->failed;
       }
       s->cv_done.notify_all();
@@ -242,14 +289,14 @@ void worker_main(aes_server* s) {
       s->cv_work.wait(lk);
       continue;
     }
-    if (free_slot < 0 || s->admit == s->next_ticket) {
+    if (free_slot < 0 || s->admit == s->filled) {
       s->cv_work.wait(lk);
       continue;
     }
     // 2. admit from the head of the queue into one batch: the ticket range [admit, t)
     const uint64_t first = s->admit;
     uint64_t t = first;
-    while (t < s->next_ticket && t - first < s->cfg.max_batch && s->inflight < s->cfg.max_inflight) {
+    while (t < s->filled && t - first < s->cfg.max_batch && s->inflight < s->cfg.max_inflight) {
       Req& q = s->at(t);
       if (needs_staging(q.r)) {
         size_t off = 0;
@@ -274,16 +321,20 @@ void worker_main(aes_server* s) {
     if (s->launches == 0 || s->t_first_launch == 0) s->t_first_launch = now_s();
     ++s->launches;
     s->launched_reqs += t - first;
-    lk.unlock();
-    const aes_status rc = issue(s, free_slot);
-    lk.lock();
-    if (rc != AES_OK) {
-      // copies queued before the failure may still read the staging: drain the stream first
+    sl.inject_fail = s->cfg.fail_every && s->launches % s->cfg.fail_every == 0;  // launches n, 2n, 3n, ...
+    if (t - first <= kInlineIssue) {
+      // a small batch is issued right here: a hand-off to the issuer thread would cost a
+      // thread wake-up, more than the batch's own host work
       lk.unlock();
-      cudaStreamSynchronize(sl.stream);
+      const aes_status rc = issue(s, free_slot);
+      if (rc != AES_OK) {
+        cudaStreamSynchronize(sl.stream);
+        retire(s, sl, now_s(), AES_REQ_FAILED);
+      }
       lk.lock();
-      retire(s, sl, now_s(), AES_REQ_FAILED);
-      s->cv_done.notify_all();
+    } else {
+      sl.pending = true;
+      s->cv_issue.notify_all();
     }
   }
 }
@@ -304,31 +355,45 @@ aes_status validate(const aes_server* s, const aes_request* r) {
   return AES_OK;
 }
 
-// Places n requests (already validated) into the ring; caller holds mu and has checked room.
-void enqueue(aes_server* s, const aes_request* reqs, size_t n, uint64_t* tickets) {
-  const double t = now_s();
-  if (s->submitted == 0 || s->t_first == 0) s->t_first = t;
+// Writes requests reqs[0..n) as the reserved tickets t0 .. t0+n-1.  The reservation makes the
+// slots this thread's alone, so no lock is held; publish() then makes them admissible.
+void fill(aes_server* s, uint64_t t0, const aes_request* reqs, size_t n, uint64_t* tickets, double t) {
   for (size_t i = 0; i < n; ++i) {
-    const uint64_t tk = s->next_ticket++;
+    const uint64_t tk = t0 + i;
     Req& q = s->at(tk);
     q.r = reqs[i];
-    q.ticket = tk;
     q.t_submit = t;
-    q.state = AES_REQ_PENDING;
     q.staged = false;
+    q.state.store(AES_REQ_PENDING, std::memory_order_relaxed);
+    q.ticket.store(tk, std::memory_order_release);
     tickets[i] = tk;
   }
-  s->submitted += n;
 }
 
-// Room for n more tickets: the queue limit, and the ring slots they land on must be free
-// (every earlier ticket that maps there has been released by a poll).
+// Moves the fill mark over every ticket now in the ring (a later reservation may have been
+// written first).  Holds mu.
+void publish(aes_server* s, uint64_t t0, size_t n) {
+  if (s->filled == t0) s->filled = t0 + n;
+  while (s->filled < s->next_ticket && s->at(s->filled).ticket.load(std::memory_order_acquire) == s->filled) ++s->filled;
+}
+
+// Reserves n tickets (room already checked).  Holds mu.
+uint64_t reserve(aes_server* s, size_t n, double t) {
+  if (s->submitted == 0 || s->t_first == 0) s->t_first = t;
+  const uint64_t t0 = s->next_ticket;
+  s->next_ticket += n;
+  s->submitted += n;
+  return t0;
+}
+
+// Room for n more tickets: the queue limit, and the ring slots they land on must be free, i.e.
+// every older ticket sharing one of those slots has been released (all tickets below `oldest`
+// have).  Holds mu.
 aes_status room_for(const aes_server* s, size_t n) {
   if (s->next_ticket - s->admit + n > s->cfg.queue_capacity)
     return set_error(AES_EAGAIN, "submission queue full (%u)", s->cfg.queue_capacity);
-  for (size_t i = 0; i < n; ++i)
-    if (s->ring[(s->next_ticket + i) & s->mask].ticket != 0)
-      return set_error(AES_EAGAIN, "no free request slot: poll finished tickets to release them");
+  if (s->next_ticket + n - 1 >= s->oldest + s->ring_size)
+    return set_error(AES_EAGAIN, "no free request slot: poll finished tickets to release them");
   return AES_OK;
 }
 
@@ -346,7 +411,14 @@ aes_status aes_server_destroy(aes_server* s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
-  if (s->worker.joinable()) s->worker.join();
+  if (s->worker.joinable()) s->worker.join();  // returns once no batch is admitted or in flight
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop_issuers = true;
+  }
+  s->cv_issue.notify_all();
+  for (std::thread& th : s->issuers)
+    if (th.joinable()) th.join();
   for (StreamSlot& sl : s->slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     if (sl.batch) aes_batch_destroy(sl.batch);
@@ -386,14 +458,24 @@ aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_s
   size_t ring = 1;
   while (ring < cfg->queue_capacity) ring <<= 1;
   try {
-    s->ring.resize(ring);
+    s->ring.reset(new Req[ring]);
     s->lat_us.reserve(std::min<size_t>(ring, size_t(1) << 22));
   } catch (...) {
     aes_server_destroy(s);
     return set_error(AES_ENOMEM, "request ring of %zu entries could not be allocated", ring);
   }
   s->mask = ring - 1;
+  s->ring_size = ring;
   s->slots.resize(cfg->nstreams);
+  try {
+    for (StreamSlot& sl : s->slots) {
+      sl.lat.reserve(cfg->max_batch);
+      sl.frees.reserve(cfg->max_batch);
+    }
+  } catch (...) {
+    aes_server_destroy(s);
+    return set_error(AES_ENOMEM, "host allocation failed");
+  }
   s->done_msgs.resize(cfg->nstreams);
   for (uint32_t i = 0; i < cfg->nstreams; ++i) {
     s->done_msgs[i] = DoneMsg{s, int(i)};
@@ -407,7 +489,13 @@ aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_s
       return st;
     }
   }
-  s->worker = std::thread(worker_main, s);
+  try {
+    for (uint32_t i = 0; i < cfg->nstreams; ++i) s->issuers.emplace_back(issuer_main, s, int(i));
+    s->worker = std::thread(worker_main, s);
+  } catch (...) {
+    aes_server_destroy(s);
+    return set_error(AES_ENOMEM, "server threads could not be started");
+  }
   *out = s;
   return AES_OK;
 }
@@ -421,7 +509,10 @@ aes_status aes_server_submit(aes_server* s, const aes_request* req, uint64_t* ti
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return set_error(AES_EINVAL, "server is shutting down");
     if ((st = room_for(s, 1)) != AES_OK) return st;
-    enqueue(s, req, 1, ticket);
+    const double t = now_s();
+    const uint64_t t0 = reserve(s, 1, t);
+    fill(s, t0, req, 1, ticket, t);
+    publish(s, t0, 1);
   }
   s->cv_work.notify_one();
   return AES_OK;
@@ -429,6 +520,7 @@ aes_status aes_server_submit(aes_server* s, const aes_request* req, uint64_t* ti
 
 aes_status aes_server_submit_many(aes_server* s, const aes_request* reqs, size_t n, uint64_t* tickets) {
   clear_error();
+  const double t = now_s();  // the submission starts now, validation included
   if (!s || (n && (!reqs || !tickets))) return set_error(AES_EINVAL, "null server, request or ticket array");
   for (size_t i = 0; i < n; ++i) {
     aes_status st = validate(s, reqs + i);
@@ -439,14 +531,27 @@ aes_status aes_server_submit_many(aes_server* s, const aes_request* reqs, size_t
     }
   }
   if (n == 0) return AES_OK;
+  // All n tickets are reserved at once (all or nothing), then written in chunks without the
+  // lock; each chunk is published as soon as it is written, so admission and launches start
+  // while the rest of the submission is still being written.
+  constexpr size_t kChunk = 4096;
+  uint64_t t0 = 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return set_error(AES_EINVAL, "server is shutting down");
     aes_status st = room_for(s, n);
     if (st != AES_OK) return st;
-    enqueue(s, reqs, n, tickets);
+    t0 = reserve(s, n, t);
   }
-  s->cv_work.notify_one();
+  for (size_t c = 0; c < n; c += kChunk) {
+    const size_t m = std::min(kChunk, n - c);
+    fill(s, t0 + c, reqs + c, m, tickets + c, t);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      publish(s, t0 + c, m);
+    }
+    s->cv_work.notify_one();
+  }
   return AES_OK;
 }
 
@@ -454,18 +559,19 @@ aes_status aes_server_poll(aes_server* s, uint64_t ticket, int64_t timeout_us, i
   clear_error();
   if (!s || !state) return set_error(AES_EINVAL, "null server or state pointer");
   std::unique_lock<std::mutex> lk(s->mu);
-  auto known = [&] { return ticket != 0 && s->at(ticket).ticket == ticket; };
+  auto known = [&] { return ticket != 0 && ticket < s->filled && s->at(ticket).ticket.load(std::memory_order_acquire) == ticket; };
   if (!known()) return set_error(AES_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
-  auto ready = [&] { return !known() || s->at(ticket).state != AES_REQ_PENDING; };
+  auto ready = [&] { return !known() || s->at(ticket).state.load(std::memory_order_acquire) != AES_REQ_PENDING; };
   if (!ready() && timeout_us != 0) {
     if (timeout_us < 0) s->cv_done.wait(lk, ready);
     else s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
   }
   if (!known()) return set_error(AES_ENOTFOUND, "ticket %llu was released by another poll", (unsigned long long)ticket);
   Req& q = s->at(ticket);
-  *state = q.state;
-  if (q.state == AES_REQ_PENDING) return set_error(AES_ETIMEDOUT, "ticket %llu still pending", (unsigned long long)ticket);
-  q.ticket = 0;  // released: the slot can take a new request
+  *state = q.state.load(std::memory_order_acquire);
+  if (*state == AES_REQ_PENDING) return set_error(AES_ETIMEDOUT, "ticket %llu still pending", (unsigned long long)ticket);
+  q.ticket.store(0, std::memory_order_release);  // released: the slot can take a new request
+  while (s->oldest < s->filled && s->at(s->oldest).ticket.load(std::memory_order_acquire) != s->oldest) ++s->oldest;
   return AES_OK;
 }
 
