@@ -84,3 +84,25 @@ def test_cbc_argument_checks(aes_lib_ready):
     assert lib.aes_cbc_crypt(ctypes.byref(ks), iv.data_ptr() + 8, 0, x.data_ptr(), x.data_ptr(), 4, 4, 0, None) == aes.AES_EINVAL
     assert lib.aes_cbc_crypt(ctypes.byref(ks), None, 0, x.data_ptr(), x.data_ptr(), 4, 4, 0, None) == aes.AES_EINVAL
     assert lib.aes_cbc_crypt(ctypes.byref(ks), iv.data_ptr(), 0, x.data_ptr(), x.data_ptr() + 16, 4, 4, 0, None) == aes.AES_EINVAL
+
+
+def test_bench_shape_2p18_messages_sampled(aes_lib_ready, orc):
+    """2^18 messages x 16 blocks (64 MiB), one IV per message: the benchmark's CBC row, in the
+    launch the benchmark times; sampled messages against the oracle, full round trip."""
+    import torch
+
+    n, m = 1 << 18, 16
+    g = torch.Generator(device="cuda").manual_seed(82)
+    x = torch.randint(0, 256, (n, 16 * m), dtype=torch.uint8, device="cuda", generator=g)
+    ivs = torch.randint(0, 256, (n, 16), dtype=torch.uint8, device="cuda", generator=g)
+    key = np.arange(16, dtype=np.uint8) * 11
+    ks = aes.aes_key_expand(key.tobytes())
+    ct = aes.cbc(x, ks, ivs, "encrypt")
+    rows = np.unique(np.concatenate([[0, 1, n // 2, n - 2, n - 1], np.random.default_rng(83).integers(0, n, 300)]))
+    tr = torch.from_numpy(rows).cuda()
+    p, c, v = x[tr].cpu().numpy(), ct[tr].cpu().numpy(), ivs[tr].cpu().numpy()
+    for k in range(rows.size):
+        assert (c[k] == orc.cbc_encrypt(key, v[k], p[k])).all(), rows[k]
+    back = aes.cbc(ct, ks, ivs, "decrypt")
+    torch.cuda.synchronize()
+    assert torch.equal(back, x)
