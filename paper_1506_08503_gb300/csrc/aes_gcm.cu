@@ -27,7 +27,7 @@
 // data.  The tree's multipliers H^(2^j) use unreplicated tables.
 //
 // Three launches on the caller's stream: set-up (one CTA: H, Cipher(J0), H^(2^j) by
-// repeated squaring, all tables, into the caller's workspace), the data pass (persistent,
+// repeated squaring, Q, all tables, into the caller's workspace), the data pass (persistent,
 // one CTA per SM: counter-mode AES with the T-table round code, a GHASH Horner step per
 // block, the in-CTA tree), and the final combine and tag.
 #include <cstring>
@@ -100,16 +100,35 @@ __device__ Be square(Be a) {
   return bxor(bxor(lo, b), bxor(mulx_small(b, 1), bxor(mulx_small(b, 2), mulx_small(b, 7))));
 }
 
-// Entry v of nibble table j for multiplier m: sum over the bits of v of m * x^(4j + b),
-// bit 3 of v standing for x^(4j).
-__device__ uint4 table_entry(Be m, int j, int v) {
-  Be base = mulx(m, 4 * j), acc{0, 0, 0, 0};
+// Entry v of nibble table j from the multiples mx[i] = M * x^i: the XOR of mx[4j + b] over
+// the bits b of v, bit 3 of v standing for x^(4j).
+__device__ __forceinline__ uint4 entry_from_multiples(const Be* mx, int j, int v) {
+  Be acc{0, 0, 0, 0};
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    if ((v >> (3 - b)) & 1) acc = bxor(acc, mx[4 * j + b]);
+  return to_le(acc);
+}
+
+// a * M for one warp (all 32 lanes, a warp-uniform) from the multiples mx[i] = M * x^i:
+// lane l adds mx[i] for the set coefficients i = 4l .. 4l+3 of a, then the lanes XOR-reduce.
+__device__ Be warp_mul(Be a, const Be* mx) {
+  const int l = int(threadIdx.x & 31u);
+  const uint32_t w = (l >> 3) == 0 ? a.w0 : (l >> 3) == 1 ? a.w1 : (l >> 3) == 2 ? a.w2 : a.w3;
+  Be acc{0, 0, 0, 0};
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    if ((v >> (3 - b)) & 1) acc = bxor(acc, base);
-    base = mulx_small(base, 1);
+    const int i = 4 * l + b;  // coefficient x^i: bit 31 - (i mod 32) of its word
+    if ((w >> (31 - (i & 31))) & 1u) acc = bxor(acc, mx[i]);
   }
-  return to_le(acc);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    acc.w0 ^= __shfl_xor_sync(0xFFFFFFFFu, acc.w0, d);
+    acc.w1 ^= __shfl_xor_sync(0xFFFFFFFFu, acc.w1, d);
+    acc.w2 ^= __shfl_xor_sync(0xFFFFFFFFu, acc.w2, d);
+    acc.w3 ^= __shfl_xor_sync(0xFFFFFFFFu, acc.w3, d);
+  }
+  return acc;
 }
 
 // y * M with M's unreplicated table (512 entries, entry j*16 + v).
@@ -191,13 +210,15 @@ struct GcmArgs {
 };
 
 // ---- set-up: H, Cipher(J0), powers, tables ------------------------------------------------
+// The T-tables serve the two cipher calls; their shared memory then holds the multiples
+// M * x^i (i < 128) of the 17 powers H^(2^j) and of Q, from which every table entry is an
+// XOR of at most four.
 template <int NR>
 __global__ void __launch_bounds__(kThreads, 1)
 gcm_setup(const KeyWords kw, uint32_t iv0, uint32_t iv1, uint32_t iv2, uint32_t T, char* work) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint4 s_he[2];
   __shared__ Be s_pow[18];
-  __shared__ Be s_q;
   fill_tables<AES_ENCRYPT>(smem);
   __syncthreads();
   const uint32_t tid = threadIdx.x;
@@ -205,26 +226,28 @@ gcm_setup(const KeyWords kw, uint32_t iv0, uint32_t iv1, uint32_t iv2, uint32_t 
     const uint4 v = tid ? make_uint4(iv0, iv1, iv2, bswap32(1u)) : make_uint4(0, 0, 0, 0);
     s_he[tid] = crypt_block<NR, AES_ENCRYPT>(v, kw, reinterpret_cast<const char*>(smem), (tid & 31u) * 4u);
   }
-  __syncthreads();
+  __syncthreads();  // the T-tables are not needed any more
   if (tid == 0) {
     Be p = to_be(s_he[0]);
     s_pow[0] = p;
     for (int j = 1; j < 18; ++j) s_pow[j] = p = square(p);
   }
   __syncthreads();
-  uint4* pow_tab = reinterpret_cast<uint4*>(work + kPowTab);
-  const int j = int(tid >> 4), v = int(tid & 15u);
-  for (int m = 0; m < kPowTables; ++m) pow_tab[m * 512 + tid] = table_entry(s_pow[m], j, v);
-  __syncthreads();  // the tables are read back below (block-wide visibility of global writes)
-  if (tid == 0) {
-    int hi = 31 - __clz(T);  // T < 2^18
-    uint4 q = to_le(s_pow[hi]);
+  Be* mx = reinterpret_cast<Be*>(smem);  // mx[m * 128 + i] = M_m * x^i; M_17 = Q
+  for (uint32_t e = tid; e < kPowTables * 128; e += kThreads) mx[e] = mulx(s_pow[e >> 7], int(e & 127u));
+  __syncthreads();
+  if (tid < 32) {  // Q = H^T, T < 2^18, as a product of the powers H^(2^b)
+    const int hi = 31 - __clz(T);
+    Be q = s_pow[hi];
     for (int b = 0; b < hi; ++b)
-      if ((T >> b) & 1u) q = mul_tab(q, pow_tab + b * 512);
-    s_q = to_be(q);
+      if ((T >> b) & 1u) q = warp_mul(q, mx + b * 128);
+    for (uint32_t i = tid; i < 128; i += 32) mx[kPowTables * 128 + i] = mulx(q, int(i));
   }
   __syncthreads();
-  const uint4 e = table_entry(s_q, j, v);
+  const int j = int(tid >> 4), v = int(tid & 15u);
+  uint4* pow_tab = reinterpret_cast<uint4*>(work + kPowTab);
+  for (int m = 0; m < kPowTables; ++m) pow_tab[m * 512 + tid] = entry_from_multiples(mx + m * 128, j, v);
+  const uint4 e = entry_from_multiples(mx + kPowTables * 128, j, v);
   uint4* qtab = reinterpret_cast<uint4*>(work + kQTab);
 #pragma unroll
   for (int c = 0; c < 8; ++c) qtab[tid * 8 + c] = e;
@@ -400,7 +423,7 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
 
   const uint64_t a = (aad_len + 15) / 16, c = (nbytes + 15) / 16, n = a + c;
   const int max_ctas = di->sms < kMaxCtas ? di->sms : kMaxCtas;
-  uint64_t want = (n + uint64_t(kThreads) * 4 - 1) / (uint64_t(kThreads) * 4);
+  const uint64_t want = (n + kThreads - 1) / kThreads;  // at least one position per thread
   const uint32_t nb = n == 0 ? 0u : uint32_t(want < 1 ? 1 : want > uint64_t(max_ctas) ? uint64_t(max_ctas) : want);
   const uint32_t T = (nb ? nb : 1u) * kThreads;
   uint32_t ivw[3];
