@@ -106,3 +106,29 @@ def test_bench_shape_2p18_messages_sampled(aes_lib_ready, orc):
     back = aes.cbc(ct, ks, ivs, "decrypt")
     torch.cuda.synchronize()
     assert torch.equal(back, x)
+
+
+@pytest.mark.parametrize("m", [1, 13, 16, 21])
+def test_staged_encrypt_ragged(aes_lib_ready, orc, m):
+    """Enough messages for the staged (shared-memory tiled) encryption kernel, a message count
+    that leaves the last warp's group partial, and lengths that leave the last stage partial."""
+    import torch
+
+    n = 152 * 512 + 37
+    g = torch.Generator(device="cuda").manual_seed(84 + m)
+    x = torch.randint(0, 256, (n, 16 * m), dtype=torch.uint8, device="cuda", generator=g)
+    ivs = torch.randint(0, 256, (n, 16), dtype=torch.uint8, device="cuda", generator=g)
+    key = np.arange(32, dtype=np.uint8) * 5
+    ks = aes.aes_key_expand(key.tobytes(), 256)
+    ct = aes.cbc(x, ks, ivs, "encrypt")
+    rows = np.unique(np.concatenate([np.arange(0, 40), np.arange(n - 40, n),
+                                     np.random.default_rng(85).integers(0, n, 200)]))
+    tr = torch.from_numpy(rows).cuda()
+    p, c, v = x[tr].cpu().numpy(), ct[tr].cpu().numpy(), ivs[tr].cpu().numpy()
+    for k in range(rows.size):
+        assert (c[k] == orc.cbc_encrypt(key, v[k], p[k])).all(), rows[k]
+    y = x.clone()
+    aes.cbc(y, ks, ivs, "encrypt", out=y)  # in place
+    torch.cuda.synchronize()
+    assert torch.equal(y, ct)
+    assert torch.equal(aes.cbc(ct, ks, ivs, "decrypt"), x)
