@@ -1,15 +1,15 @@
 // aes_batched.cu -- host side of the batched launch: descriptor staging, the cached CUDA
-// graph that replays [descriptor copy -> encrypt kernel -> decrypt kernel], the autotuner
-// and aes_crypt_batched.
+// graph that replays the two-direction kernel, the autotuner and aes_crypt_batched.
 //
 // Per run the host splits the messages by direction, drops empty ones, writes 32-byte
 // descriptors plus each message's first block in the direction's concatenated block space
-// into pinned staging, copies them to the device on the batch's own copy stream (so the
-// upload overlaps whatever the caller's stream is still running, e.g. the previous batch),
-// and launches the graph [encrypt kernel -> decrypt kernel] on the caller's stream behind that
-// copy.  The graph is built once per (buffer, shape); later runs only patch the kernel
-// arguments (cudaGraphExecKernelNodeSetParams) when they change and switch off a direction
-// without work.  Two staging/device buffer pairs alternate; a run waits for the run that used
+// into pinned staging, cuts each direction into per-warp slices of equal work (blocks x
+// rounds), splits the CTAs between the directions in proportion to their work, copies all of
+// it to the device on the batch's own copy stream (so the upload overlaps whatever the
+// caller's stream is still running, e.g. the previous batch), and launches the graph [one
+// kernel, both directions] on the caller's stream behind that copy.  The graph is built once
+// per shape; later runs patch the kernel arguments (cudaGraphExecKernelNodeSetParams) when
+// they change.  Two staging/device buffer pairs alternate; a run waits for the run that used
 // its pair two calls ago, so descriptors are never overwritten while a kernel reads them.
 #include <algorithm>
 #include <cstdio>
@@ -42,17 +42,12 @@ struct Slot {
   cudaEvent_t copied = nullptr;  // this slot's descriptors are on the device
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t kenc = nullptr, kdec = nullptr;
+  cudaGraphNode_t kernel = nullptr;
   int g_threads = 0, g_bpl = 0;
-  // what the instantiated graph currently holds, to skip redundant updates
-  unsigned g_grid[2] = {0, 0};
-  BatchDir g_bd[2] = {};
-  uint64_t g_in = 0, g_out = 0;
-  int g_enabled[2] = {-1, -1};
 };
 
 struct Layout {
-  size_t enc_msgs, dec_msgs, enc_start, dec_start, enc_warp, dec_warp, end;
+  size_t enc_msgs, dec_msgs, enc_start, dec_start, enc_gb, dec_gb, enc_warp, dec_warp, end;
 };
 
 // wmax: most warps a launch can have (SMs x 512 threads / 32)
@@ -62,29 +57,48 @@ Layout layout(size_t nenc, size_t ndec, size_t wmax) {
   l.dec_msgs = l.enc_msgs + nenc * sizeof(BatchMsg);
   l.enc_start = l.dec_msgs + ndec * sizeof(BatchMsg);
   l.dec_start = l.enc_start + (nenc + 1) * sizeof(uint64_t);
-  l.enc_warp = l.dec_start + (ndec + 1) * sizeof(uint64_t);
+  l.enc_gb = l.dec_start + (ndec + 1) * sizeof(uint64_t);
+  l.dec_gb = l.enc_gb + (wmax + 1) * sizeof(uint64_t);
+  l.enc_warp = l.dec_gb + (wmax + 1) * sizeof(uint64_t);
   l.dec_warp = l.enc_warp + wmax * sizeof(uint32_t);
   l.end = l.dec_warp + wmax * sizeof(uint32_t);
   return l;
 }
 
-// First message of every warp's slice: warp w of nw starts at block floor(total * w / nw).
-// The quotient is advanced incrementally (no division per warp).
-void warp_starts(const uint64_t* start, size_t nmsgs, uint64_t total, uint64_t nw, uint32_t* out) {
+// Work of a direction in round-blocks (a block of an Nr-round key costs Nr).
+uint64_t work_of(const BatchMsg* m, size_t n, const int8_t* rounds) {
+  uint64_t w = 0;
+  for (size_t i = 0; i < n; ++i) w += m[i].nblocks * uint64_t(rounds[m[i].key_idx]);
+  return w;
+}
+
+// Cuts a direction's block space into nw slices of equal work: warp w starts at the block
+// where the running work reaches floor(W * w / nw).  gb[w] is that block (gb[nw] = the
+// direction's total), msg[w] the message holding it.  Targets advance incrementally.
+void weighted_slices(const BatchMsg* m, const uint64_t* start, size_t n, const int8_t* rounds, uint64_t W,
+                     uint64_t nw, uint64_t* gb, uint32_t* msg) {
   if (nw == 0) return;
-  const uint64_t step = total / nw, rem = total % nw;
-  uint64_t lo = 0, r = 0;
-  size_t m = 0;
+  const uint64_t step = W / nw, rem = W % nw;
+  uint64_t t = 0, r = 0, acc = 0;  // acc: work before message i
+  size_t i = 0;
   for (uint64_t w = 0; w < nw; ++w) {
-    while (m + 1 < nmsgs && start[m + 1] <= lo) ++m;
-    out[w] = uint32_t(m);
-    lo += step;
+    uint64_t rw = uint64_t(rounds[m[i].key_idx]);
+    while (i + 1 < n && acc + m[i].nblocks * rw <= t) {
+      acc += m[i].nblocks * rw;
+      ++i;
+      rw = uint64_t(rounds[m[i].key_idx]);
+    }
+    const uint64_t off = std::min<uint64_t>((t - acc) / rw, m[i].nblocks - 1);
+    gb[w] = start[i] + off;
+    msg[w] = uint32_t(i);
+    t += step;
     r += rem;
     if (r >= nw) {
-      ++lo;
+      ++t;
       r -= nw;
     }
   }
+  gb[nw] = start[n];
 }
 
 }  // namespace
@@ -117,18 +131,21 @@ void free_slot(Slot& s) {
 struct KernelArgs {
   uint64_t in;
   uint64_t out;
-  BatchDir bd;
+  BatchDir be, bd;
   const PoolEntry* pool;
-  void* ptrs[4];
+  uint32_t ge;
+  void* ptrs[6];
   void fix() {
     ptrs[0] = &in;
     ptrs[1] = &out;
-    ptrs[2] = &bd;
-    ptrs[3] = &pool;
+    ptrs[2] = &be;
+    ptrs[3] = &bd;
+    ptrs[4] = &pool;
+    ptrs[5] = &ge;
   }
 };
 
-cudaKernelNodeParams kernel_params(TTBatchedFn fn, unsigned grid, int threads, size_t smem, KernelArgs& a) {
+cudaKernelNodeParams kernel_params(TTDualFn fn, unsigned grid, int threads, size_t smem, KernelArgs& a) {
   a.fix();
   cudaKernelNodeParams p{};
   p.func = reinterpret_cast<void*>(fn);
@@ -140,26 +157,20 @@ cudaKernelNodeParams kernel_params(TTBatchedFn fn, unsigned grid, int threads, s
   return p;
 }
 
-aes_status build_graph(aes_batch* b, Slot& s, const cudaKernelNodeParams& pe, const cudaKernelNodeParams& pd) {
+aes_status build_graph(aes_batch* b, Slot& s, const cudaKernelNodeParams& p) {
   if (s.exec) { cudaGraphExecDestroy(s.exec); s.exec = nullptr; }
   if (s.graph) { cudaGraphDestroy(s.graph); s.graph = nullptr; }
   cudaError_t e;
   if ((e = cudaGraphCreate(&s.graph, 0)) != cudaSuccess) return cuda_error(e, "cudaGraphCreate");
-  if ((e = cudaGraphAddKernelNode(&s.kenc, s.graph, nullptr, 0, &pe)) != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode(enc)");
-  if ((e = cudaGraphAddKernelNode(&s.kdec, s.graph, &s.kenc, 1, &pd)) != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode(dec)");
+  if ((e = cudaGraphAddKernelNode(&s.kernel, s.graph, nullptr, 0, &p)) != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode");
   if ((e = cudaGraphInstantiate(&s.exec, s.graph, 0)) != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
   s.g_threads = b->threads;
   s.g_bpl = b->bpl;
-  s.g_enabled[0] = s.g_enabled[1] = -1;
   return AES_OK;
 }
 
-bool same_dir(const BatchDir& a, const BatchDir& b) {
-  return a.msgs == b.msgs && a.start == b.start && a.warp_msg == b.warp_msg && a.total == b.total && a.nmsgs == b.nmsgs;
-}
-
 // The kernels' dynamic shared-memory limit is raised once per device and kernel.
-aes_status ensure_smem_attr(TTBatchedFn f, size_t smem) {
+aes_status ensure_smem_attr(TTDualFn f, size_t smem) {
   static std::mutex mu;
   static std::vector<std::pair<int, const void*>> done;
   int dev = -1;
@@ -203,55 +214,42 @@ aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
 
   const DeviceInfo* di = current_device_info();
   if (!di) return AES_ECUDA;
-  TTBatchedFn fe = ttable_batched_enc(b->threads, b->bpl), fd = ttable_batched_dec(b->threads, b->bpl);
-  if (!fe || !fd) return set_error(AES_EINVAL, "shape (%d threads, %d blocks per lane) is not compiled", b->threads, b->bpl);
-  const size_t se = ttable_smem_bytes(AES_ENCRYPT), sd = ttable_smem_bytes(AES_DECRYPT);
-  aes_status ast = ensure_smem_attr(fe, se);
-  if (ast == AES_OK) ast = ensure_smem_attr(fd, sd);
+  TTDualFn fn = ttable_batched_dual(b->threads, b->bpl);
+  if (!fn) return set_error(AES_EINVAL, "shape (%d threads, %d blocks per lane) is not compiled", b->threads, b->bpl);
+  const size_t smem = ttable_smem_bytes(AES_DECRYPT);
+  aes_status ast = ensure_smem_attr(fn, smem);
   if (ast != AES_OK) return ast;
-  // one CTA per SM (fewer when a direction has less than one block per thread)
+  // one CTA per SM (fewer when there is less than one block per thread), split between the
+  // directions in proportion to their work in round-blocks
+  const int8_t* rounds = b->pool->nr;
+  const uint64_t we = work_of(em, nenc, rounds), wd = work_of(dm, ndec, rounds);
   const uint64_t per_cta = uint64_t(b->threads);
-  const unsigned ge = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(di->sms, (te + per_cta - 1) / per_cta)));
-  const unsigned gd = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(di->sms, (td + per_cta - 1) / per_cta)));
-  const uint64_t nwe = uint64_t(ge) * (b->threads / 32), nwd = uint64_t(gd) * (b->threads / 32);
+  uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>(di->sms, (te + td + per_cta - 1) / per_cta));
+  if (te && td) G = std::max<uint64_t>(G, 2);
+  uint64_t ge = 0;
+  if (!td) ge = G;
+  else if (te) ge = std::min<uint64_t>(G - 1, std::max<uint64_t>(1, (G * we + (we + wd) / 2) / (we + wd)));
+  const uint64_t gd = G - ge;
+  const uint64_t wpc = uint64_t(b->threads / 32), nwe = ge * wpc, nwd = gd * wpc;
   if (nwe > b->wmax || nwd > b->wmax) return set_error(AES_ECUDA, "device has more SMs than the batch was sized for");
-  warp_starts(es, nenc, te, nwe, reinterpret_cast<uint32_t*>(h + L.enc_warp));
-  warp_starts(ds, ndec, td, nwd, reinterpret_cast<uint32_t*>(h + L.dec_warp));
-  KernelArgs ae{in_base, out_base,
-                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.enc_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.enc_start),
-                         reinterpret_cast<const uint32_t*>(s.dev + L.enc_warp), te, uint32_t(nenc), 0u},
-                b->pool->entries, {}};
-  KernelArgs ad{in_base, out_base,
-                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.dec_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.dec_start),
-                         reinterpret_cast<const uint32_t*>(s.dev + L.dec_warp), td, uint32_t(ndec), 0u},
-                b->pool->entries, {}};
-  const cudaKernelNodeParams pe = kernel_params(fe, ge, b->threads, se, ae);
-  const cudaKernelNodeParams pd = kernel_params(fd, gd, b->threads, sd, ad);
+  weighted_slices(em, es, nenc, rounds, we, te ? nwe : 0, reinterpret_cast<uint64_t*>(h + L.enc_gb),
+                  reinterpret_cast<uint32_t*>(h + L.enc_warp));
+  weighted_slices(dm, ds, ndec, rounds, wd, td ? nwd : 0, reinterpret_cast<uint64_t*>(h + L.dec_gb),
+                  reinterpret_cast<uint32_t*>(h + L.dec_warp));
+  KernelArgs a{in_base, out_base,
+               BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.enc_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.enc_start),
+                        reinterpret_cast<const uint32_t*>(s.dev + L.enc_warp), te, uint32_t(nenc), 0u,
+                        reinterpret_cast<const uint64_t*>(s.dev + L.enc_gb)},
+               BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.dec_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.dec_start),
+                        reinterpret_cast<const uint32_t*>(s.dev + L.dec_warp), td, uint32_t(ndec), 0u,
+                        reinterpret_cast<const uint64_t*>(s.dev + L.dec_gb)},
+               b->pool->entries, uint32_t(ge), {}};
+  const cudaKernelNodeParams p = kernel_params(fn, unsigned(G), b->threads, smem, a);
   if (!s.exec || s.g_threads != b->threads || s.g_bpl != b->bpl) {
-    aes_status st = build_graph(b, s, pe, pd);
+    aes_status st = build_graph(b, s, p);
     if (st != AES_OK) return st;
-  } else {
-    const bool same_io = s.g_in == in_base && s.g_out == out_base;
-    if (!(same_io && s.g_grid[0] == ge && same_dir(s.g_bd[0], ae.bd)))
-      if ((e = cudaGraphExecKernelNodeSetParams(s.exec, s.kenc, &pe)) != cudaSuccess) return cuda_error(e, "cudaGraphExecKernelNodeSetParams(enc)");
-    if (!(same_io && s.g_grid[1] == gd && same_dir(s.g_bd[1], ad.bd)))
-      if ((e = cudaGraphExecKernelNodeSetParams(s.exec, s.kdec, &pd)) != cudaSuccess) return cuda_error(e, "cudaGraphExecKernelNodeSetParams(dec)");
-  }
-  s.g_in = in_base;
-  s.g_out = out_base;
-  s.g_grid[0] = ge;
-  s.g_grid[1] = gd;
-  s.g_bd[0] = ae.bd;
-  s.g_bd[1] = ad.bd;
-  // a direction without work is switched off in the instantiated graph (no empty launch)
-  const int en_e = te ? 1 : 0, en_d = td ? 1 : 0;
-  if (s.g_enabled[0] != en_e) {
-    if ((e = cudaGraphNodeSetEnabled(s.exec, s.kenc, unsigned(en_e))) != cudaSuccess) return cuda_error(e, "cudaGraphNodeSetEnabled");
-    s.g_enabled[0] = en_e;
-  }
-  if (s.g_enabled[1] != en_d) {
-    if ((e = cudaGraphNodeSetEnabled(s.exec, s.kdec, unsigned(en_d))) != cudaSuccess) return cuda_error(e, "cudaGraphNodeSetEnabled");
-    s.g_enabled[1] = en_d;
+  } else if ((e = cudaGraphExecKernelNodeSetParams(s.exec, s.kernel, &p)) != cudaSuccess) {
+    return cuda_error(e, "cudaGraphExecKernelNodeSetParams");
   }
   if ((e = cudaMemcpyAsync(s.dev, s.host, L.end, cudaMemcpyHostToDevice, b->copy_stream)) != cudaSuccess)
     return cuda_error(e, "descriptor upload");

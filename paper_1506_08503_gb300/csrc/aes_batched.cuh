@@ -3,10 +3,12 @@
 // The paper keeps one key schedule per message (the tensor K, Section II) and processes all
 // messages of a matrix together.  Here the messages of one direction are laid end to end in a
 // virtual block space of G blocks (message m covers [start[m], start[m+1])), and that space
-// is cut into one equal contiguous slice per warp, so every warp gets the same amount of work
-// whatever the length distribution, without atomics or per-tile searches.  Round keys sit in
-// registers and are reloaded from the device key pool only when the key changes.  AES-128,
-// -192 and -256 messages can share a launch: the round count is read with the key.
+// is cut into one contiguous slice per warp.  The host places the cuts so that every warp has
+// the same work in blocks x rounds (an AES-256 block costs 14 rounds, an AES-128 block 10),
+// whatever the length and key-size mix, without atomics or per-tile searches.  Round keys sit
+// in registers and are reloaded from the device key pool only when the key changes.  AES-128,
+// -192 and -256 messages share a launch: the round count is read with the key.  Encryption
+// and decryption share it too: the CTAs are split between them in proportion to their work.
 #pragma once
 #include "aes_ttable.cuh"
 
@@ -93,20 +95,26 @@ __device__ __forceinline__ uint4 crypt_rt(uint4 v, const uint32_t (&kw)[kMaxRoun
 // (Measured alternatives that were slower: the next window loaded into registers one window
 // ahead; the first window issued before the table fill; a separate loop for whole windows,
 // whose second copy of the unrolled rounds costs more in instruction fetch than it saves.)
+// The work of CTA `cta` of the `ncta` CTAs given to one direction.
 template <int DIR, int THREADS, int U>
-__global__ void __launch_bounds__(THREADS, 1)
-tt_batched_kernel(uint64_t in_base, uint64_t out_base, const BatchDir bd, const PoolEntry* pool) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  if (bd.total == 0) return;  // grid-uniform, before any barrier
+__device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base, const BatchDir& bd,
+                                             const PoolEntry* pool, uint32_t cta, uint32_t ncta, uint32_t* smem) {
+  if (bd.total == 0) return;  // CTA-uniform, before any barrier
   fill_tables<DIR>(smem);
   __syncthreads();
   const char* sm = reinterpret_cast<const char*>(smem);
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lc = lane * 4u;
-  const uint64_t nwarps = uint64_t(gridDim.x) * (THREADS / 32);
-  const uint64_t w = (uint64_t(blockIdx.x) * THREADS + threadIdx.x) >> 5;
-  const uint64_t hi = bd.total * (w + 1) / nwarps;
-  uint64_t gb = bd.total * w / nwarps;
+  const uint64_t nwarps = uint64_t(ncta) * (THREADS / 32);
+  const uint64_t w = (uint64_t(cta) * THREADS + threadIdx.x) >> 5;
+  uint64_t gb, hi;
+  if (bd.warp_gb) {
+    gb = ldg64(bd.warp_gb + w);
+    hi = ldg64(bd.warp_gb + w + 1);
+  } else {
+    hi = bd.total * (w + 1) / nwarps;
+    gb = bd.total * w / nwarps;
+  }
   if (gb >= hi) return;  // warp-uniform; no barrier follows
 
   uint32_t kw[kMaxRounds + 1][4];
@@ -155,16 +163,23 @@ tt_batched_kernel(uint64_t in_base, uint64_t out_base, const BatchDir bd, const 
   }
 }
 
-// Compiled shapes the autotuner may pick: (CTA threads, blocks per lane per window).  One
-// CTA per SM: the tables take 128-192 KiB of shared memory.
-template <int DIR>
-TTBatchedFn select_batched(int threads, int u) {
-  if (threads == 512 && u == 1) return tt_batched_kernel<DIR, 512, 1>;
-  if (threads == 512 && u == 2) return tt_batched_kernel<DIR, 512, 2>;
-  if (threads == 512 && u == 4) return tt_batched_kernel<DIR, 512, 4>;
-  if (threads == 384 && u == 4) return tt_batched_kernel<DIR, 384, 4>;
-  if (threads == 256 && u == 4) return tt_batched_kernel<DIR, 256, 4>;
-  return nullptr;
+template <int DIR, int THREADS, int U>
+__global__ void __launch_bounds__(THREADS, 1)
+tt_batched_kernel(uint64_t in_base, uint64_t out_base, const BatchDir bd, const PoolEntry* pool) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  batched_body<DIR, THREADS, U>(in_base, out_base, bd, pool, blockIdx.x, gridDim.x, smem);
+}
+
+// Both directions in one launch: CTAs [0, ge) encrypt, the others decrypt, so the two run
+// side by side instead of one after the other (one tail, one launch).  Each CTA fills only
+// its own direction's tables; the dynamic shared memory is sized for decryption.
+template <int THREADS, int U>
+__global__ void __launch_bounds__(THREADS, 1)
+tt_batched_dual(uint64_t in_base, uint64_t out_base, const BatchDir be, const BatchDir bdd, const PoolEntry* pool,
+                uint32_t ge) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  if (blockIdx.x < ge) batched_body<AES_ENCRYPT, THREADS, U>(in_base, out_base, be, pool, blockIdx.x, ge, smem);
+  else batched_body<AES_DECRYPT, THREADS, U>(in_base, out_base, bdd, pool, blockIdx.x - ge, gridDim.x - ge, smem);
 }
 
 }  // namespace tt

@@ -95,7 +95,9 @@ static_assert(sizeof(BatchMsg) == 32, "batch descriptors are 32 bytes");
 // Work of one direction: messages laid end to end; start[m] is the first block of message m
 // in that virtual block space (nmsgs + 1 entries, the last = total).
 // warp_msg[w] (optional, may be null) is the message holding warp w's first block when the
-// kernel runs with exactly nwarps = grid * threads / 32 warps.
+// kernel runs with exactly the warps the table was made for; warp_gb (optional, nwarps + 1
+// entries) gives each warp's first block, so that the host can balance the slices by work
+// (blocks x rounds) rather than by blocks.  Without it every warp takes an equal block range.
 struct BatchDir {
   const BatchMsg* msgs;
   const uint64_t* start;
@@ -103,14 +105,17 @@ struct BatchDir {
   uint64_t total;
   uint32_t nmsgs;
   uint32_t pad;
+  const uint64_t* warp_gb;
 };
 
 // Kernel arguments: input and output base addresses as integers (the server passes 0 and
 // absolute block numbers), the direction's work, the key pool.
 using TTBatchedFn = void (*)(uint64_t, uint64_t, const BatchDir, const PoolEntry*);
+// Both directions in one launch: the first `ge` CTAs encrypt, the rest decrypt.
+using TTDualFn = void (*)(uint64_t, uint64_t, const BatchDir, const BatchDir, const PoolEntry*, uint32_t);
 // Compiled shapes (CTA threads, blocks per lane per window); nullptr if not compiled.
-TTBatchedFn ttable_batched_enc(int threads, int blocks_per_lane);
-TTBatchedFn ttable_batched_dec(int threads, int blocks_per_lane);
+TTDualFn ttable_batched_dual(int threads, int blocks_per_lane);
+TTDualFn ttable_batched_dual_wide(int threads, int blocks_per_lane);  // the U = 4 shapes
 
 }  // namespace aesgb
 
