@@ -88,9 +88,23 @@ aes_status aes_decrypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, con
                               void* d_out, size_t nblocks, void* cuda_stream);
 
 /* Same, with the direction (AES_ENCRYPT / AES_DECRYPT) and kernel family (AES_IMPL_*)
- * chosen explicitly.  An unknown dir or impl is AES_EINVAL. */
+ * chosen explicitly.  An unknown dir or impl is AES_EINVAL.  AES_IMPL_AUTO takes the choice
+ * aes_autotune_blocks made for this device, direction and round count, else the T-tables
+ * with 512-thread CTAs and two blocks in flight per thread. */
 aes_status aes_crypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, const void* d_in,
                             void* d_out, size_t nblocks, int dir, int impl, void* cuda_stream);
+
+/* Tunes AES_IMPL_AUTO for the current device, `dir` and ks->nr: times every compiled
+ * candidate on d_in -> d_out (nblocks blocks, device, 16-byte aligned; d_out is overwritten):
+ * the T-table kernel with CTAs of 512 threads and 1, 2 or 4 blocks in flight per thread, 256
+ * threads and 4, 1024 threads and 1 or 2, and the bitsliced kernel (32 blocks per thread).
+ * The fastest serves later AES_IMPL_AUTO calls in this process.  If cache_path is not NULL
+ * the choice is also recorded in that JSON file, keyed by device name, direction, round count
+ * and floor(log2(nblocks)); an existing entry is used without timing.  Writes the choice to
+ * *impl (AES_IMPL_TTABLE or AES_IMPL_BITSLICE), *threads and *unroll when not NULL.
+ * Synchronous: it waits for its timing launches.  nblocks = 0 is AES_EINVAL. */
+aes_status aes_autotune_blocks(const aes_key_schedule* ks, const void* d_in, void* d_out, size_t nblocks, int dir,
+                               const char* cache_path, int* impl, int* threads, int* unroll, void* cuda_stream);
 
 /* The paper's CBC mode over whole messages (Section II; App. A1 encryption, App. A4
  * decryption).  d_in and d_out (device) hold an nmsgs x (16 * blocks_per_msg) byte matrix, one

@@ -110,6 +110,8 @@ _SIGS: dict[str, tuple] = {
     "aes_cbc_crypt": (_I, [_KSP, _VP, _I, _VP, _VP, _SZ, _SZ, _I, _VP]),
     "aes_ctr_crypt": (_I, [_KSP, _U8P, _VP, _VP, _SZ, _VP]),
     "aes_scan_equal": (_I, [_VP, _SZ, _U8P, _VP, _SZ, _VP, _VP]),
+    "aes_autotune_blocks": (_I, [_KSP, _VP, _VP, _SZ, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                 ctypes.POINTER(_I), _VP]),
     "aes_gcm_workspace_bytes": (_SZ, []),
     "aes_gcm_crypt": (_I, [_KSP, _U8P, _SZ, _VP, _SZ, _VP, _VP, _SZ, _I, _VP, _VP, _SZ, _VP]),
     "aes_crypt_batched_noalloc": (_I, [_KSP, ctypes.c_uint32, _VP, _SZ, _VP, _VP, _SZ, _VP]),
@@ -271,6 +273,17 @@ def ctr(x, ks: aes_key_schedule, ctr0: bytes, out=None, stream=None):
         out = torch.empty_like(x)
     aes_ctr_crypt(ks, ctr0, x.data_ptr(), out.data_ptr(), n, stream)
     return out
+
+
+def aes_autotune_blocks(ks: aes_key_schedule, d_in: int, d_out: int, nblocks: int, dir, cache_path=None,
+                        stream=None) -> dict:
+    """Tunes AES_IMPL_AUTO for this device, direction and round count; returns the choice."""
+    i, t, u = _I(), _I(), _I()
+    cp = None if cache_path is None else str(cache_path).encode()
+    _check(lib().aes_autotune_blocks(ctypes.byref(ks), d_in, d_out, nblocks, _dir(dir), cp, ctypes.byref(i),
+                                     ctypes.byref(t), ctypes.byref(u), _stream_ptr(stream)))
+    return {"impl": {AES_IMPL_TTABLE: "ttable", AES_IMPL_BITSLICE: "bitslice"}.get(i.value, i.value),
+            "threads": t.value, "blocks_per_thread": u.value}
 
 
 def aes_gcm_workspace_bytes() -> int:

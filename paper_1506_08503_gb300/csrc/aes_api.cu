@@ -156,9 +156,10 @@ aes_status aes_crypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, const
   if (a != b && a < b + bytes && b < a + bytes)
     return set_error(AES_EINVAL, "input and output overlap without being identical");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  TTConfig cfg;
+  if (impl == AES_IMPL_AUTO && !tuned_choice(dir, ks->nr, &impl, &cfg)) impl = AES_IMPL_TTABLE;
   if (impl == AES_IMPL_BITSLICE) return launch_bitslice(dir, *ks, iv, d_in, d_out, nblocks, st, BSConfig{});
   const KeyWords kw = dir == AES_ENCRYPT ? enc_key_words(*ks, iv) : dec_key_words(*ks, iv);
-  TTConfig cfg;
   return launch_ttable(dir, ks->nr, kw, d_in, d_out, nblocks, st, cfg);
 }
 

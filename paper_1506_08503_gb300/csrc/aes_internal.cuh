@@ -65,6 +65,9 @@ aes_status launch_ttable(int dir, int nr, const KeyWords& kw, const void* d_in, 
                          size_t nblocks, cudaStream_t stream, const TTConfig& cfg);
 // The bitsliced kernels take the plain schedule (they run the paper's inverse-cipher order,
 // not the equivalent inverse cipher); the IV is folded into round key 0.
+// The tuned choice for AES_IMPL_AUTO on the current device (aes_autotune_blocks); false when
+// none was tuned (then the default T-table shape is used).
+bool tuned_choice(int dir, int nr, int* impl, TTConfig* cfg);
 aes_status launch_bitslice(int dir, const aes_key_schedule& ks, const uint8_t* iv, const void* d_in,
                            void* d_out, size_t nblocks, cudaStream_t stream, const BSConfig& cfg);
 

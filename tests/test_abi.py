@@ -136,3 +136,15 @@ def test_gcm_argument_checks_before_any_cuda_call(aes):
     assert call(aad=base + 48, aad_len=32) == aes.AES_EINVAL  # output overlaps the AAD
     assert call(n=16 * (1 << 32)) == aes.AES_EINVAL  # beyond 2^32 - 2 blocks
     assert call(src=None, dst=None) == aes.AES_EINVAL
+
+
+def test_autotune_argument_checks_before_any_cuda_call(aes):
+    lib = aes.lib()
+    ks = aes.aes_key_expand(bytes(16))
+    kp = ctypes.byref(ks)
+    base = 1 << 40  # never dereferenced
+    assert lib.aes_autotune_blocks(kp, base, base + 4096, 0, 0, None, None, None, None, None) == aes.AES_EINVAL
+    assert lib.aes_autotune_blocks(kp, base, base + 4096, 4, 2, None, None, None, None, None) == aes.AES_EINVAL
+    assert lib.aes_autotune_blocks(kp, base + 8, base + 4096, 4, 0, None, None, None, None, None) == aes.AES_EINVAL
+    assert lib.aes_autotune_blocks(kp, base, base + 16, 4, 0, None, None, None, None, None) == aes.AES_EINVAL
+    assert lib.aes_autotune_blocks(None, base, base + 4096, 4, 0, None, None, None, None, None) == aes.AES_EINVAL
