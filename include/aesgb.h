@@ -160,14 +160,17 @@ aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* iv, size_t i
 aes_status aes_scan_equal(const void* d_column, size_t nrecords, const uint8_t* needle, uint64_t* d_matches,
                           size_t max_matches, uint64_t* d_count, void* cuda_stream);
 
-/* Same cipher on HOST buffers: the library copies the data to the device in 64 MiB chunks,
- * runs the kernel and copies the result back, overlapping the three on its own streams.
+/* Same cipher on HOST buffers.  On a device whose kernels may access host memory directly
+ * (pageable access through the host page tables, e.g. Grace-Blackwell over NVLink-C2C) and
+ * with both buffers 16-byte aligned, the kernel reads h_in and writes h_out itself, on
+ * cuda_stream.  Otherwise the library copies the data to the device in 64 MiB chunks, runs
+ * the kernel and copies the result back, overlapping the three on its own streams.
  *   h_in, h_out  host pointers (pinned memory gives full copy bandwidth; pageable works,
- *                slower), nblocks * 16 bytes, no alignment rule; in place allowed
- *   cuda_stream  the copies start after the work already queued on this stream
- * Blocks until h_out holds the result.  The first call on a device allocates the staging
- * buffers (3 x 64 MiB, kept until process exit); AES_ENOMEM if that fails.  Calls on one
- * device are serialised. */
+ *                slower, on the copy path), nblocks * 16 bytes; in place allowed
+ *   cuda_stream  the work starts after the work already queued on this stream
+ * Blocks until h_out holds the result.  The first copy-path call on a device allocates the
+ * staging buffers (3 x 64 MiB, kept until process exit); AES_ENOMEM if that fails.  Copy-path
+ * calls on one device are serialised. */
 aes_status aes_crypt_host(const aes_key_schedule* ks, const uint8_t* iv, const void* h_in, void* h_out,
                           size_t nblocks, int dir, int impl, void* cuda_stream);
 

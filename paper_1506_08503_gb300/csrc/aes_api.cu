@@ -51,8 +51,15 @@ const DeviceInfo* current_device_info() {
   }
   cudaDeviceProp p;
   if ((e = cudaGetDeviceProperties(&p, dev)) != cudaSuccess) { cuda_error(e, "cudaGetDeviceProperties"); return nullptr; }
+  int pageable = 0, host_tables = 0;
+  if ((e = cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev)) != cudaSuccess) {
+    cuda_error(e, "cudaDeviceGetAttribute");
+    return nullptr;
+  }
   d.sms = sms;
   d.smem_optin = optin;
+  d.host_direct = pageable == 1 && host_tables == 1;
   std::snprintf(d.name, sizeof(d.name), "%s", p.name);
   d.device = dev;
   return &d;

@@ -1,6 +1,12 @@
-// aes_host.cu -- encryption/decryption of HOST buffers: the library stages the data through
-// device memory in chunks, overlapping host->device copies, the cipher kernel and
-// device->host copies on three streams.
+// aes_host.cu -- encryption/decryption of HOST buffers.
+//
+// Where kernels may load and store host memory themselves (pageable access through the host
+// page tables, as Grace-Blackwell offers over NVLink-C2C) and both buffers are 16-byte
+// aligned, the cipher kernel runs on the host buffers directly: every byte crosses the link
+// once in each direction, as with copies, but without staging or copy engines (measured on a
+// GB300: 170 GB/s each way against 144-157 GB/s for the copy pipeline).  Otherwise the library
+// stages the data through device memory in chunks, overlapping host->device copies, the
+// cipher kernel and device->host copies on three streams.
 #include <cstring>
 #include <mutex>
 
@@ -65,6 +71,14 @@ extern "C" aes_status aes_crypt_host(const aes_key_schedule* ks, const uint8_t* 
   if (a != b && a < b + bytes && b < a + bytes)
     return set_error(AES_EINVAL, "input and output overlap without being identical");
 
+  const DeviceInfo* di = current_device_info();
+  if (!di) return AES_ECUDA;
+  if (di->host_direct && ((a | b) & 15u) == 0) {
+    aes_status st = aes_crypt_blocks(ks, iv, h_in, h_out, nblocks, dir, impl, cuda_stream);
+    if (st != AES_OK) return st;
+    const cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? AES_OK : cuda_error(e, "host-buffer kernel");
+  }
   Staging* s = nullptr;
   aes_status st = staging_for_current(&s);
   if (st != AES_OK) return st;

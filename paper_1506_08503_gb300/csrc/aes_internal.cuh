@@ -31,6 +31,9 @@ struct DeviceInfo {
   int device = -1;
   int sms = 0;
   int smem_optin = 0;  // max dynamic shared memory per block (bytes)
+  // kernels may load and store any host memory (pageable access through the host's page
+  // tables, as on Grace-Blackwell over NVLink-C2C)
+  bool host_direct = false;
   char name[256] = {0};
 };
 // Info for the current device (cached per device).  Returns nullptr and sets the error on

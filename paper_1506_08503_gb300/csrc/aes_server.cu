@@ -5,9 +5,10 @@
 // thread keeps a FIFO of submitted requests and, whenever one of its CUDA streams is idle,
 // admits as many queued requests as the in-flight limit, the batch size and the free staging
 // memory allow, and starts them as ONE batched launch on that stream:
-//   host-sourced payloads are copied into the staging arena (or straight into a device
-//   destination), the batch graph runs the cipher in place or device-to-device, and host
-//   destinations are copied back; a host callback at the end of the stream marks the batch's
+//   host payloads that the kernel can reach itself (a device with direct access to host
+//   memory, 16-byte aligned buffers) are read and written in place; other host-sourced
+//   payloads are copied into the staging arena (or straight into a device destination), the
+//   batch graph runs the cipher, and other host destinations are copied back; a host callback at the end of the stream marks the batch's
 //   requests complete, frees their staging and wakes the thread and any waiting poll.
 // Requests arriving while batches run are admitted into the next free stream's batch, so the
 // device works on several batches at once and nobody waits for a full drain.
@@ -116,8 +117,6 @@ struct DoneMsg {
   int slot;
 };
 
-// A host destination needs device staging; a device destination doubles as the staging.
-bool needs_staging(const aes_request& r) { return !r.dst_on_device; }
 
 }  // namespace
 
@@ -127,6 +126,7 @@ struct aes_server {
   int device = -1;
   uint8_t* arena_base = nullptr;
   Arena arena;
+  bool host_direct = false;  // kernels may load and store host memory (see DeviceInfo)
   std::vector<StreamSlot> slots;
   std::vector<DoneMsg> done_msgs;
 
@@ -154,6 +154,22 @@ struct aes_server {
 };
 
 namespace {
+
+// A buffer the kernel reads or writes itself: device memory, or host memory on a device that
+// accesses host memory directly (16-byte aligned, for 128-bit accesses).  Other host buffers
+// are copied through the staging arena.
+bool src_direct(const aes_server* s, const aes_request& r) {
+  return r.src_on_device || (s->host_direct && (reinterpret_cast<uintptr_t>(r.src) & 15u) == 0);
+}
+bool dst_direct(const aes_server* s, const aes_request& r) {
+  return r.dst_on_device || (s->host_direct && (reinterpret_cast<uintptr_t>(r.dst) & 15u) == 0);
+}
+// Staging holds the output for a destination that is not direct, and the input for a source
+// that is not direct when the destination is not device memory (a device destination takes
+// the copied input and is enciphered in place).
+bool needs_staging(const aes_server* s, const aes_request& r) {
+  return !dst_direct(s, r) || (!src_direct(s, r) && !r.dst_on_device);
+}
 
 // Finishes a slot's batch: every request's state becomes `state` (DONE or FAILED), then the
 // counters, latencies and staging frees are applied under the mutex in one step.  The slot's
@@ -211,7 +227,7 @@ aes_status issue(aes_server* s, int i) {
   for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
     const Req& q = s->at(tk);
     const aes_request& r = q.r;
-    if (!r.src_on_device) {
+    if (!src_direct(s, r)) {
       void* to = r.dst_on_device ? r.dst : static_cast<void*>(s->arena_base + q.stage_off);
       if ((e = cudaMemcpyAsync(to, r.src, r.length, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_error(e, "H2D");
     }
@@ -226,8 +242,9 @@ aes_status issue(aes_server* s, int i) {
       const Req& q = s->at(tk);
       const aes_request& r = q.r;
       const uint64_t stage = reinterpret_cast<uint64_t>(s->arena_base + q.stage_off);
-      const uint64_t out_addr = r.dst_on_device ? reinterpret_cast<uint64_t>(r.dst) : stage;
-      const uint64_t in_addr = r.src_on_device ? reinterpret_cast<uint64_t>(r.src) : out_addr;
+      const uint64_t out_addr = dst_direct(s, r) ? reinterpret_cast<uint64_t>(r.dst) : stage;
+      const uint64_t in_addr = src_direct(s, r) ? reinterpret_cast<uint64_t>(r.src)
+                               : r.dst_on_device ? reinterpret_cast<uint64_t>(r.dst) : stage;
       const BatchMsg d{r.key_idx, 0u, in_addr / 16, out_addr / 16, r.length / 16};
       if (r.dir == AES_ENCRYPT) em[ie++] = d;
       else dm[id++] = d;
@@ -237,7 +254,7 @@ aes_status issue(aes_server* s, int i) {
   if (rc != AES_OK) return rc;
   for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
     const Req& q = s->at(tk);
-    if (!q.r.dst_on_device)
+    if (!dst_direct(s, q.r))
       if ((e = cudaMemcpyAsync(q.r.dst, s->arena_base + q.stage_off, q.r.length, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_error(e, "D2H");
   }
@@ -298,7 +315,7 @@ void worker_main(aes_server* s) {
     uint64_t t = first;
     while (t < s->filled && t - first < s->cfg.max_batch && s->inflight < s->cfg.max_inflight) {
       Req& q = s->at(t);
-      if (needs_staging(q.r)) {
+      if (needs_staging(s, q.r)) {
         size_t off = 0;
         if (!s->arena.alloc(q.r.length, &off)) break;  // wait for staging to free up
         q.staged = true;
@@ -349,7 +366,7 @@ aes_status validate(const aes_server* s, const aes_request* r) {
     return set_error(AES_EINVAL, "device buffers must be 16-byte aligned");
   if (size_t(r->key_idx) >= s->pool->capacity || s->pool->nr[r->key_idx] == 0)
     return set_error(AES_EINVAL, "key slot %u is not loaded", r->key_idx);
-  if (needs_staging(*r) && ((r->length + 255) & ~uint64_t(255)) > s->cfg.hbm_budget)
+  if (needs_staging(s, *r) && ((r->length + 255) & ~uint64_t(255)) > s->cfg.hbm_budget)
     return set_error(AES_ENOMEM, "request of %llu bytes exceeds the staging budget of %llu bytes",
                      (unsigned long long)r->length, (unsigned long long)s->cfg.hbm_budget);
   return AES_OK;
@@ -361,7 +378,7 @@ inline bool quick_ok(const aes_server* s, const aes_request& r) {
   const uintptr_t mis = ((r.src_on_device ? reinterpret_cast<uintptr_t>(r.src) : 0u) |
                          (r.dst_on_device ? reinterpret_cast<uintptr_t>(r.dst) : 0u)) & 15u;
   const bool key_ok = size_t(r.key_idx) < s->pool->capacity && s->pool->nr[r.key_idx] != 0;
-  const bool stage_ok = r.dst_on_device || ((r.length + 255) & ~uint64_t(255)) <= s->cfg.hbm_budget;
+  const bool stage_ok = !needs_staging(s, r) || ((r.length + 255) & ~uint64_t(255)) <= s->cfg.hbm_budget;
   return (r.dir <= 1u) & (r.length != 0) & ((r.length & 15u) == 0) & (r.src != nullptr) & (r.dst != nullptr) &
          (mis == 0) & key_ok & stage_ok;
 }
@@ -466,6 +483,14 @@ aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_s
     return set_error(AES_ENOMEM, "staging arena cudaMalloc failed: %s", cudaGetErrorString(e));
   }
   s->arena.reset(cfg->hbm_budget);
+  {
+    const DeviceInfo* di = current_device_info();
+    if (!di) {
+      aes_server_destroy(s);
+      return AES_ECUDA;
+    }
+    s->host_direct = di->host_direct;
+  }
   size_t ring = 1;
   while (ring < cfg->queue_capacity) ring <<= 1;
   try {

@@ -55,6 +55,31 @@ def test_requests_match_oracle_host_and_device_buffers(aes_lib_ready, orc):
         assert st["launches"] >= 1 and st["mean_batch"] >= 1
 
 
+def test_host_buffers_staged_and_direct(aes_lib_ready, orc):
+    """Host payloads 16-byte aligned (read and written by the kernel itself where the device
+    reaches host memory directly) and 8 bytes off (copied through the staging arena), in every
+    combination for source and destination, in one mix."""
+    rng = np.random.default_rng(46)
+    pool, keys = make_pool(rng)
+    with pool, aes.Server(pool, hbm_budget=64 << 20, nstreams=4, max_batch=32) as srv:
+        items = []
+        for i in range(160):
+            n = int(rng.integers(1, 3000))
+            data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
+            so, do = 8 * (i % 2), 8 * ((i // 2) % 2)
+            src_buf = np.empty(16 * n + 16, dtype=np.uint8)
+            dst_buf = np.empty(16 * n + 16, dtype=np.uint8)
+            src_buf[so:so + 16 * n] = data
+            k, d = int(rng.integers(0, len(keys))), int(rng.integers(0, 2))
+            t = srv.submit(k, d, src_buf.ctypes.data + so, dst_buf.ctypes.data + do, 16 * n, False, False)
+            items.append((t, data, src_buf, dst_buf, do, k, d))
+        for t, data, src_buf, dst_buf, do, k, d in items:
+            assert srv.poll(t, 10_000_000) == aes.AES_REQ_DONE
+            assert (dst_buf[do:do + data.size] == oracle_crypt(orc, keys[k], data, d)).all()
+        st = srv.stats()
+        assert st["completed"] == 160 and st["failed"] == 0
+
+
 def test_result_is_the_same_alone_and_in_the_mix(aes_lib_ready):
     import torch
 
@@ -65,20 +90,22 @@ def test_result_is_the_same_alone_and_in_the_mix(aes_lib_ready):
         alone = np.empty_like(probe)
         t = srv.submit(5, 0, probe.ctypes.data, alone.ctypes.data, probe.size, False, False)
         assert srv.poll(t) == aes.AES_REQ_DONE
-        # the same request inside a stream of 600 others of every size and direction
-        others, tickets = [], []
+        # the same request inside a stream of 600 others of every size and direction, arriving
+        # in two waves: the probe heads the second wave, queued while the first is on the GPU
         mixed = np.empty_like(probe)
+        others = []
         for i in range(600):
-            if i == 300:
-                tickets.append(srv.submit(5, 0, probe.ctypes.data, mixed.ctypes.data, probe.size, False, False))
-            n = int(rng.integers(1, 4000))
-            a = rng.integers(0, 256, 16 * n, dtype=np.uint8)
-            b = np.empty_like(a)
-            others.append((a, b))
-            tickets.append(srv.submit(int(rng.integers(0, 8)), int(rng.integers(0, 2)), a.ctypes.data, b.ctypes.data,
-                                      a.size, False, False))
+            a = rng.integers(0, 256, 16 * int(rng.integers(1, 4000)), dtype=np.uint8)
+            others.append((int(rng.integers(0, 8)), int(rng.integers(0, 2)), a, np.empty_like(a)))
+        reqs = np.zeros(601, dtype=aes.request_dtype())
+        rows = [(k, d, a.ctypes.data, b.ctypes.data, a.size) for k, d, a, b in others]
+        rows.insert(300, (5, 0, probe.ctypes.data, mixed.ctypes.data, probe.size))
+        cols = list(zip(*rows))
+        for name, col in zip(("key_idx", "dir", "src", "dst", "length"), cols):
+            reqs[name] = np.array(col, dtype=reqs.dtype[name])
+        tickets = list(srv.submit_many(reqs[:300])) + list(srv.submit_many(reqs[300:]))
         for t in tickets:
-            assert srv.poll(t) == aes.AES_REQ_DONE
+            assert srv.poll(int(t)) == aes.AES_REQ_DONE
         assert (alone == mixed).all()
         # and the same as the plain single-key entry point
         ks = aes.aes_key_expand(keys[5].tobytes())
@@ -122,10 +149,11 @@ def test_backpressure_and_bounded_waits(aes_lib_ready):
         with pytest.raises(aes.AesError) as ei:
             srv.poll(123456789, 0)
         assert ei.value.status == aes.AES_ENOTFOUND
-        # a request larger than the whole staging budget is refused up front
+        # a request larger than the whole staging budget is refused up front (a buffer 8 bytes
+        # off 16-byte alignment is always staged, also where kernels reach host memory directly)
         huge = np.empty(16 << 20, dtype=np.uint8)
         with pytest.raises(aes.AesError) as ei:
-            srv.submit(0, 0, huge.ctypes.data, huge.ctypes.data, huge.size, False, False)
+            srv.submit(0, 0, huge.ctypes.data + 8, huge.ctypes.data + 8, huge.size - 16, False, False)
         assert ei.value.status == aes.AES_ENOMEM
         for bad in [(99, 0, 64), (0, 2, 64), (0, 0, 24), (0, 0, 0)]:
             with pytest.raises(aes.AesError) as ei:
