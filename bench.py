@@ -681,6 +681,14 @@ def run_ours(args):
         cpu = {"value": 2 * s * 16 / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {s} blocks of the 1 GiB seed-1 workload, encrypt then decrypt",
                "seconds": dt, "gpu_matches_oracle_on_sample": bool((gpu_ct == oct_).all() and (opt == sample).all())}
+        # the sensor column (10^7 records) on the same cores: a bounded sample of its records
+        col = workloads.sensor_records(2, 10_000_000)
+        for name, kb in (("aes128", col.key128), ("aes256", col.key256)):
+            _, k = oracle_rate(orc, kb, col.records, cores, max(1.0, args.cpu_seconds / 4), 10_000_000)
+            t = time.perf_counter()
+            orc.encrypt_blocks(kb, col.records[: k * 16], threads=cores)
+            cpu[f"sensor_{name}_encrypt_gbs"] = k * 16 / (time.perf_counter() - t) / 1e9
+            cpu[f"sensor_{name}_records"] = k
 
     if rank == 0:
         line = {
