@@ -141,10 +141,11 @@ aes_status aes_ctr_crypt(const aes_key_schedule* ks, const uint8_t* ctr0, const 
  *   d_tag      device, 16 bytes, any alignment: receives the tag.  On decryption it is the
  *              tag computed from the ciphertext: the caller compares it with the received tag
  *              before trusting the plaintext
- *   d_work     device workspace of at least aes_gcm_workspace_bytes() bytes, 16-byte aligned,
- *              owned by the caller; calls that share a workspace must be ordered on one
- *              stream, and it must not overlap any other buffer
- * Three kernel launches on cuda_stream (set-up, data pass, combine); asynchronous. */
+ *   d_work     device workspace of at least aes_gcm_workspace_bytes() bytes (a few KiB: one
+ *              partial sum per CTA and a ticket), 16-byte aligned, owned by the caller; calls
+ *              that share a workspace must be ordered on one stream, and it must not overlap
+ *              any other buffer
+ * One kernel launch on cuda_stream (after a 4-byte memset of the ticket); asynchronous. */
 size_t aes_gcm_workspace_bytes(void);
 aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* iv, size_t iv_len, const void* d_aad,
                          size_t aad_len, const void* d_in, void* d_out, size_t nbytes, int dir, uint8_t* d_tag,

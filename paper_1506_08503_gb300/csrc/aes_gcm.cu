@@ -26,10 +26,12 @@
 // lookup of a warp is exactly four conflict-free shared-memory wavefronts, whatever the
 // data.  The tree's multipliers H^(2^j) use unreplicated tables.
 //
-// Three launches on the caller's stream: set-up (one CTA: H, Cipher(J0), H^(2^j) by
-// repeated squaring, Q, all tables, into the caller's workspace), the data pass (persistent,
-// one CTA per SM: counter-mode AES with the T-table round code, a GHASH Horner step per
-// block, the in-CTA tree), and the final combine and tag.
+// One launch on the caller's stream.  Every CTA derives what it needs itself (H and
+// Cipher(J0), H^(2^j) by repeated squaring, Q, the tables, from multiples M * x^i held in
+// shared memory), runs the data pass (persistent, one CTA per SM: counter-mode AES with the
+// T-table round code and a GHASH Horner step per block) and its tree; the CTA that finishes
+// last, found with an atomic ticket (no CTA waits for another), combines the partial sums
+// and writes the tag.  The caller's workspace holds only the partial sums and the ticket.
 #include <cstring>
 
 #include "aes_ttable.cuh"
@@ -40,13 +42,10 @@ namespace {
 using namespace tt;
 
 // ---- workspace layout (bytes) ------------------------------------------------------------
-constexpr size_t kQTab = 0;                           // Q table, 8 copies: 64 KiB
-constexpr size_t kPowTab = 65536;                     // tables of H^(2^j), j = 0..16
-constexpr int kPowTables = 17;
-constexpr size_t kVals = kPowTab + kPowTables * 8192;  // H, Cipher(J0)
-constexpr size_t kParts = kVals + 256;                // one partial sum per CTA
 constexpr int kMaxCtas = 256;
-constexpr size_t kWorkBytes = kParts + kMaxCtas * 16;
+constexpr size_t kParts = 0;                        // one partial sum per CTA
+constexpr size_t kCounter = kParts + kMaxCtas * 16;  // finished-CTA ticket (uint32)
+constexpr size_t kWorkBytes = kCounter + 16;
 constexpr int kThreads = 512;
 constexpr uint32_t kAesSmem = 2 * kRegion;            // encryption T-tables (128 KiB)
 constexpr uint32_t kMainSmem = kAesSmem + 65536;      // + replicated Q table
@@ -209,70 +208,78 @@ struct GcmArgs {
   int decrypt;
 };
 
-// ---- set-up: H, Cipher(J0), powers, tables ------------------------------------------------
-// The T-tables serve the two cipher calls; their shared memory then holds the multiples
-// M * x^i (i < 128) of the 17 powers H^(2^j) and of Q, from which every table entry is an
-// XOR of at most four.
-template <int NR>
+// Builds, into tabs[k * 512 ..], the nibble tables of the multipliers ms[k] (k < count), using
+// mx (count * 128 entries) as scratch for the multiples M * x^i.  All threads of the CTA
+// call it; it ends with a barrier.
+__device__ void build_tables(const Be* ms, int count, Be* mx, uint4* tabs) {
+  for (uint32_t e = threadIdx.x; e < uint32_t(count) * 128u; e += blockDim.x) mx[e] = mulx(ms[e >> 7], int(e & 127u));
+  __syncthreads();
+  for (uint32_t e = threadIdx.x; e < uint32_t(count) * 512u; e += blockDim.x)
+    tabs[e] = entry_from_multiples(mx + (e >> 9) * 128, int((e >> 4) & 31u), int(e & 15u));
+  __syncthreads();
+}
+
+// ---- the whole GCM in one launch ------------------------------------------------------------
+// Every CTA: the AES T-tables; H = Cipher(0), Cipher(J0); the powers H^(2^j) by squaring;
+// Q = H^T; Q's table (8 copies, beside the T-tables); then the data pass (counter-mode AES
+// and one GHASH Horner step per position); then the tree over its 512 threads.  The CTA that
+// finishes last (an atomic ticket; nobody waits) combines the CTAs' partial sums and writes
+// the tag.
+template <int NR, int U>
 __global__ void __launch_bounds__(kThreads, 1)
-gcm_setup(const KeyWords kw, uint32_t iv0, uint32_t iv1, uint32_t iv2, uint32_t T, char* work) {
+gcm_kernel(const GcmArgs g, const KeyWords kw, char* work, uint8_t* tag, uint64_t abits, uint64_t cbits) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint4 s_he[2];
   __shared__ Be s_pow[18];
+  __shared__ Be s_ms[9];
+  __shared__ uint4 s_warp[kThreads / 32];
+  __shared__ bool s_last;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u;
+  char* smc = reinterpret_cast<char*>(smem);
+  const char* sm = smc;
+  const uint32_t lc = lane * 4u;
   fill_tables<AES_ENCRYPT>(smem);
   __syncthreads();
-  const uint32_t tid = threadIdx.x;
   if (tid < 2) {
-    const uint4 v = tid ? make_uint4(iv0, iv1, iv2, bswap32(1u)) : make_uint4(0, 0, 0, 0);
-    s_he[tid] = crypt_block<NR, AES_ENCRYPT>(v, kw, reinterpret_cast<const char*>(smem), (tid & 31u) * 4u);
+    const uint4 v = tid ? make_uint4(g.iv0, g.iv1, g.iv2, bswap32(1u)) : make_uint4(0, 0, 0, 0);
+    s_he[tid] = crypt_block<NR, AES_ENCRYPT>(v, kw, sm, lc);
   }
-  __syncthreads();  // the T-tables are not needed any more
+  __syncthreads();
   if (tid == 0) {
     Be p = to_be(s_he[0]);
     s_pow[0] = p;
     for (int j = 1; j < 18; ++j) s_pow[j] = p = square(p);
   }
   __syncthreads();
-  Be* mx = reinterpret_cast<Be*>(smem);  // mx[m * 128 + i] = M_m * x^i; M_17 = Q
-  for (uint32_t e = tid; e < kPowTables * 128; e += kThreads) mx[e] = mulx(s_pow[e >> 7], int(e & 127u));
+  // Q = H^T (T = gridDim.x * 512 < 2^18) from the multiples of the factors H^(2^b), kept in
+  // the Q region until Q's own table is written there
+  const uint32_t T = gridDim.x * kThreads;
+  Be* qscratch = reinterpret_cast<Be*>(smc + kAesSmem);  // 18 x 128 multiples (36 KiB) at most
+  for (uint32_t e = tid; e < 18u * 128u; e += kThreads)
+    if ((T >> (e >> 7)) & 1u) qscratch[e] = mulx(s_pow[e >> 7], int(e & 127u));
   __syncthreads();
-  if (tid < 32) {  // Q = H^T, T < 2^18, as a product of the powers H^(2^b)
+  if (tid < 32) {
     const int hi = 31 - __clz(T);
     Be q = s_pow[hi];
     for (int b = 0; b < hi; ++b)
-      if ((T >> b) & 1u) q = warp_mul(q, mx + b * 128);
-    for (uint32_t i = tid; i < 128; i += 32) mx[kPowTables * 128 + i] = mulx(q, int(i));
+      if ((T >> b) & 1u) q = warp_mul(q, qscratch + b * 128);
+    if (tid == 0) s_ms[0] = q;
   }
   __syncthreads();
-  const int j = int(tid >> 4), v = int(tid & 15u);
-  uint4* pow_tab = reinterpret_cast<uint4*>(work + kPowTab);
-  for (int m = 0; m < kPowTables; ++m) pow_tab[m * 512 + tid] = entry_from_multiples(mx + m * 128, j, v);
-  const uint4 e = entry_from_multiples(mx + kPowTables * 128, j, v);
-  uint4* qtab = reinterpret_cast<uint4*>(work + kQTab);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) qtab[tid * 8 + c] = e;
-  if (tid < 2) reinterpret_cast<uint4*>(work + kVals)[tid] = s_he[tid];
-}
-
-// ---- data pass ------------------------------------------------------------------------------
-template <int NR, int U>
-__global__ void __launch_bounds__(kThreads, 1)
-gcm_main(const GcmArgs g, const KeyWords kw, char* work) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint4 s_warp[kThreads / 32];
-  fill_tables<AES_ENCRYPT>(smem);
+  Be* qmx = qscratch + 18 * 128;  // Q's multiples, after the factors' (still inside the region)
+  for (uint32_t i = tid; i < 128; i += kThreads) qmx[i] = mulx(s_ms[0], int(i));
+  __syncthreads();
+  const uint4 qe = entry_from_multiples(qmx, int(tid >> 4), int(tid & 15u));
+  __syncthreads();  // every entry is read before the table overwrites the scratch
   {
-    const uint4* src = reinterpret_cast<const uint4*>(work + kQTab);
-    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(smem) + kAesSmem);
-    for (uint32_t i = threadIdx.x; i < 65536 / 16; i += kThreads) dst[i] = src[i];
+    uint4* qtab = reinterpret_cast<uint4*>(smc + kAesSmem);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) qtab[tid * 8 + c] = qe;
   }
   __syncthreads();
-  const char* sm = reinterpret_cast<const char*>(smem);
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t lc = lane * 4u;
   const char* qb = sm + kAesSmem + (lane & 7u) * 16u;
-  const uint64_t T = uint64_t(gridDim.x) * kThreads;
-  const uint64_t t = uint64_t(blockIdx.x) * kThreads + threadIdx.x;
+  const uint64_t TT = T;
+  const uint64_t t = uint64_t(blockIdx.x) * kThreads + tid;
   const uint64_t cblocks = (g.len + 15) / 16;
 
   uint4 y = make_uint4(0, 0, 0, 0);
@@ -282,7 +289,7 @@ gcm_main(const GcmArgs g, const KeyWords kw, char* work) {
     uint64_t idx[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint64_t p = t + uint64_t(k + u) * T;
+      const uint64_t p = t + uint64_t(k + u) * TT;
       kind[u] = 0;
       idx[u] = 0;
       x[u] = make_uint4(0, 0, 0, 0);
@@ -325,43 +332,43 @@ gcm_main(const GcmArgs g, const KeyWords kw, char* work) {
     }
   }
 
-  // In-CTA tree: sum_i Y_i H^(511 - i) over the CTA's threads.
-  __syncthreads();  // the AES and Q tables are no longer needed
-  uint4* tabs = reinterpret_cast<uint4*>(smem);
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(work + kPowTab);
-    for (uint32_t i = threadIdx.x; i < 9 * 512; i += kThreads) tabs[i] = src[i];
-  }
+  // In-CTA tree: sum_i Y_i H^(511 - i) over the CTA's threads, with the tables of H^(2^j),
+  // j = 0..8, built where the T-tables were (multiples as scratch in the Q region).
   __syncthreads();
+  uint4* tabs = reinterpret_cast<uint4*>(smc);
+  Be* mx = reinterpret_cast<Be*>(smc + kAesSmem);
+  build_tables(s_pow, 9, mx, tabs);
   y = lane_tree(y, tabs, 5);
-  if (lane == 0) s_warp[threadIdx.x >> 5] = y;
+  if (lane == 0) s_warp[tid >> 5] = y;
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (tid < 32) {
     uint4 w = lane < kThreads / 32 ? s_warp[lane] : make_uint4(0, 0, 0, 0);
     w = lane_tree(w, tabs + 5 * 512, 4);
-    if (lane == 0) reinterpret_cast<uint4*>(work + kParts)[blockIdx.x] = w;
+    if (lane == 0) {
+      reinterpret_cast<uint4*>(work + kParts)[blockIdx.x] = w;
+      __threadfence();  // the partial is visible device-wide before the ticket is taken
+      const unsigned prev = atomicAdd(reinterpret_cast<unsigned*>(work + kCounter), 1u);
+      s_last = prev == gridDim.x - 1;
+    }
   }
-}
+  __syncthreads();
+  if (!s_last) return;  // CTA-uniform; no barrier follows in the other CTAs
+  __threadfence();
 
-// ---- combine and tag -------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 1)
-gcm_final(const char* work, uint32_t nb, uint64_t abits, uint64_t cbits, uint8_t* tag) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint4 s_warp[8];
-  uint4* tabs = reinterpret_cast<uint4*>(smem);  // H^(2^9) .. H^(2^16), then H
-  const uint4* pow_tab = reinterpret_cast<const uint4*>(work + kPowTab);
-  for (uint32_t i = threadIdx.x; i < 8 * 512; i += 256) tabs[i] = pow_tab[9 * 512 + i];
-  for (uint32_t i = threadIdx.x; i < 512; i += 256) tabs[8 * 512 + i] = pow_tab[i];
+  // The last CTA: CTA b's partial at slot 256 - nb + b carries (H^512)^(255 - slot); a tree
+  // over the 256 slots with the tables of H^(2^9) .. H^(2^16), then the tag.
+  if (tid < 8) s_ms[tid] = s_pow[9 + tid];
+  if (tid == 8) s_ms[8] = s_pow[0];
   __syncthreads();
-  // CTA b sits at slot 256 - nb + b, so slot s carries the power (H^512)^(255 - s).
-  const uint32_t s = threadIdx.x, lane = s & 31u;
-  const uint4* parts = reinterpret_cast<const uint4*>(work + kParts);
-  uint4 v = s >= kMaxCtas - nb ? parts[s - (kMaxCtas - nb)] : make_uint4(0, 0, 0, 0);
-  v = lane_tree(v, tabs, 5);
-  if (lane == 0) s_warp[s >> 5] = v;
+  build_tables(s_ms, 9, mx, tabs);  // tabs[0..7]: H^(2^9..2^16), tabs[8]: H
+  const uint32_t nb = gridDim.x;
+  uint4 v = make_uint4(0, 0, 0, 0);
+  if (tid < kMaxCtas && tid >= kMaxCtas - nb) v = __ldcg(reinterpret_cast<const uint4*>(work + kParts) + (tid - (kMaxCtas - nb)));
+  if (tid < kMaxCtas) v = lane_tree(v, tabs, 5);
+  if (tid < kMaxCtas && lane == 0) s_warp[tid >> 5] = v;
   __syncthreads();
-  if (s < 32) {
-    uint4 w = lane < 8 ? s_warp[lane] : make_uint4(0, 0, 0, 0);
+  if (tid < 32) {
+    uint4 w = lane < kMaxCtas / 32 ? s_warp[lane] : make_uint4(0, 0, 0, 0);
     w = lane_tree(w, tabs + 5 * 512, 3);
     if (lane == 0) {
       const uint4* h_tab = tabs + 8 * 512;
@@ -369,18 +376,34 @@ gcm_final(const char* work, uint32_t nb, uint64_t abits, uint64_t cbits, uint8_t
       const uint4 L = make_uint4(bswap32(uint32_t(abits >> 32)), bswap32(uint32_t(abits)), bswap32(uint32_t(cbits >> 32)),
                                  bswap32(uint32_t(cbits)));
       const uint4 S = mul_tab(xor4(gsum, L), h_tab);
-      const uint4 ej0 = reinterpret_cast<const uint4*>(work + kVals)[1];
-      const uint4 t = xor4(ej0, S);
-      const uint32_t tw[4] = {t.x, t.y, t.z, t.w};
+      const uint4 tg = xor4(s_he[1], S);
+      const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
 #pragma unroll
       for (int b = 0; b < 16; ++b) tag[b] = uint8_t(tw[b >> 2] >> (8 * (b & 3)));
+      *reinterpret_cast<unsigned*>(work + kCounter) = 0u;  // ready for the next call on this workspace
     }
   }
 }
 
+// No hashed block at all (empty AAD and data): the tag is Cipher(J0) + (0 + L) * H with L = 0,
+// i.e. Cipher(J0).  One thread.
+template <int NR>
+__global__ void __launch_bounds__(kThreads, 1) gcm_empty_kernel(const KeyWords kw, uint32_t iv0, uint32_t iv1, uint32_t iv2,
+                                                               uint8_t* tag) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  fill_tables<AES_ENCRYPT>(smem);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint4 e = crypt_block<NR, AES_ENCRYPT>(make_uint4(iv0, iv1, iv2, bswap32(1u)), kw,
+                                                 reinterpret_cast<const char*>(smem), 0u);
+    const uint32_t tw[4] = {e.x, e.y, e.z, e.w};
+    for (int b = 0; b < 16; ++b) tag[b] = uint8_t(tw[b >> 2] >> (8 * (b & 3)));
+  }
+}
+
 constexpr int kUnroll = 2;
-using SetupFn = void (*)(const KeyWords, uint32_t, uint32_t, uint32_t, uint32_t, char*);
-using MainFn = void (*)(const GcmArgs, const KeyWords, char*);
+using GcmFn = void (*)(const GcmArgs, const KeyWords, char*, uint8_t*, uint64_t, uint64_t);
+using EmptyFn = void (*)(const KeyWords, uint32_t, uint32_t, uint32_t, uint8_t*);
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
@@ -432,35 +455,34 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   char* work = static_cast<char*>(d_work);
 
-  SetupFn setup = ks->nr == 10 ? gcm_setup<10> : ks->nr == 12 ? gcm_setup<12> : gcm_setup<14>;
-  MainFn main_k = ks->nr == 10 ? gcm_main<10, kUnroll> : ks->nr == 12 ? gcm_main<12, kUnroll> : gcm_main<14, kUnroll>;
-  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(setup), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kAesSmem));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(main_k), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMainSmem));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(gcm_final), cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * 8192);
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(GCM)");
-
-  setup<<<1, kThreads, kAesSmem, st>>>(kw, ivw[0], ivw[1], ivw[2], T, work);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM set-up launch");
-  if (nb) {
-    GcmArgs g;
-    g.in = static_cast<const uint4*>(d_in);
-    g.out = static_cast<uint4*>(d_out);
-    g.aad = static_cast<const uint8_t*>(d_aad);
-    g.K = uint32_t((n + T - 1) / T);
-    g.z = uint64_t(g.K) * T - n;
-    g.a = a;
-    g.aad_len = aad_len;
-    g.len = nbytes;
-    g.iv0 = ivw[0];
-    g.iv1 = ivw[1];
-    g.iv2 = ivw[2];
-    g.decrypt = dir == AES_DECRYPT;
-    main_k<<<nb, kThreads, kMainSmem, st>>>(g, kw, work);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM data-pass launch");
+  cudaError_t e;
+  if (nb == 0) {  // nothing hashed: the tag is Cipher(J0)
+    EmptyFn k0 = ks->nr == 10 ? gcm_empty_kernel<10> : ks->nr == 12 ? gcm_empty_kernel<12> : gcm_empty_kernel<14>;
+    if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k0), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kAesSmem))) != cudaSuccess)
+      return cuda_error(e, "cudaFuncSetAttribute(GCM)");
+    k0<<<1, kThreads, kAesSmem, st>>>(kw, ivw[0], ivw[1], ivw[2], d_tag);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM launch");
+    return AES_OK;
   }
-  gcm_final<<<1, 256, 9 * 8192, st>>>(work, nb, uint64_t(aad_len) * 8u, uint64_t(nbytes) * 8u, d_tag);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM final launch");
+  GcmFn k = ks->nr == 10 ? gcm_kernel<10, kUnroll> : ks->nr == 12 ? gcm_kernel<12, kUnroll> : gcm_kernel<14, kUnroll>;
+  if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMainSmem))) != cudaSuccess)
+    return cuda_error(e, "cudaFuncSetAttribute(GCM)");
+  // the finished-CTA ticket starts at zero (the last CTA also puts it back)
+  if ((e = cudaMemsetAsync(work + kCounter, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(GCM ticket)");
+  GcmArgs g;
+  g.in = static_cast<const uint4*>(d_in);
+  g.out = static_cast<uint4*>(d_out);
+  g.aad = static_cast<const uint8_t*>(d_aad);
+  g.K = uint32_t((n + T - 1) / T);
+  g.z = uint64_t(g.K) * T - n;
+  g.a = a;
+  g.aad_len = aad_len;
+  g.len = nbytes;
+  g.iv0 = ivw[0];
+  g.iv1 = ivw[1];
+  g.iv2 = ivw[2];
+  g.decrypt = dir == AES_DECRYPT;
+  k<<<nb, kThreads, kMainSmem, st>>>(g, kw, work, d_tag, uint64_t(aad_len) * 8u, uint64_t(nbytes) * 8u);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM launch");
   return AES_OK;
 }
