@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "aes_internal.cuh"
 
@@ -63,6 +64,49 @@ const DeviceInfo* current_device_info() {
   std::snprintf(d.name, sizeof(d.name), "%s", p.name);
   d.device = dev;
   return &d;
+}
+
+namespace {
+struct KernelFact {
+  int device;
+  const void* fn;
+  size_t smem;
+  int threads;  // 0 for the shared-memory attribute, else an occupancy entry
+  int value;
+};
+std::mutex g_fact_mu;
+std::vector<KernelFact> g_facts;
+}  // namespace
+
+aes_status ensure_kernel_smem(const void* fn, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_fact_mu);
+  for (const KernelFact& f : g_facts)
+    if (f.device == dev && f.fn == fn && f.threads == 0 && f.smem >= bytes) return AES_OK;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes))) != cudaSuccess)
+    return cuda_error(e, "cudaFuncSetAttribute");
+  g_facts.push_back(KernelFact{dev, fn, bytes, 0, 0});
+  return AES_OK;
+}
+
+aes_status kernel_ctas_per_sm(const void* fn, int threads, size_t smem, int* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_fact_mu);
+  for (const KernelFact& f : g_facts)
+    if (f.device == dev && f.fn == fn && f.threads == threads && f.smem == smem) {
+      *out = f.value;
+      return AES_OK;
+    }
+  int n = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem)) != cudaSuccess)
+    return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  g_facts.push_back(KernelFact{dev, fn, smem, threads, n});
+  *out = n;
+  return AES_OK;
 }
 
 // ---- keys -------------------------------------------------------------------------------

@@ -169,21 +169,8 @@ aes_status build_graph(aes_batch* b, Slot& s, const cudaKernelNodeParams& p) {
   return AES_OK;
 }
 
-// The kernels' dynamic shared-memory limit is raised once per device and kernel.
-aes_status ensure_smem_attr(TTDualFn f, size_t smem) {
-  static std::mutex mu;
-  static std::vector<std::pair<int, const void*>> done;
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
-  std::lock_guard<std::mutex> lk(mu);
-  for (const auto& d : done)
-    if (d.first == dev && d.second == reinterpret_cast<const void*>(f)) return AES_OK;
-  if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
-    return cuda_error(e, "cudaFuncSetAttribute(batched)");
-  done.emplace_back(dev, reinterpret_cast<const void*>(f));
-  return AES_OK;
-}
+// The kernels' dynamic shared-memory limit, raised once per device and kernel.
+aes_status ensure_smem_attr(TTDualFn f, size_t smem) { return ensure_kernel_smem(reinterpret_cast<const void*>(f), smem); }
 
 }  // namespace
 

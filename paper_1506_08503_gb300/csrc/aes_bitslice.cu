@@ -263,8 +263,9 @@ aes_status launch_bitslice(int dir, const aes_key_schedule& ks, const uint8_t* i
   bs::Masks km;
   for (int r = 0; r <= ks.nr; ++r) bs::fill_masks(km, ks, r, r == 0 ? iv : nullptr);  // IV rides on K0
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(k), bs::kThreads, 0);
-  if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  aes_status ast = kernel_ctas_per_sm(reinterpret_cast<const void*>(k), bs::kThreads, 0, &per_sm);
+  if (ast != AES_OK) return ast;
+  cudaError_t e;
   if (per_sm < 1) per_sm = 1;
   const size_t tiles = (nblocks + bs::kTile - 1) / bs::kTile;
   const size_t want = (tiles + (bs::kThreads / 32) - 1) / (bs::kThreads / 32);

@@ -184,8 +184,9 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   const bool staged = dir == AES_ENCRYPT && nmsgs >= uint64_t(di->sms) * kStagedThreads;
   CbcKernel k = staged ? pick_staged(ks->nr) : pick(dir, ks->nr);
   const size_t smem = ttable_smem_bytes(dir) + (staged ? size_t(kStagedThreads / 32) * kTileBytes : 0);
-  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(CBC)");
+  aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k), smem);
+  if (ast != AES_OK) return ast;
+  cudaError_t e;
   unsigned threads = 512u;
   uint64_t work = uint64_t(nmsgs) * blocks_per_msg;
   if (staged) {

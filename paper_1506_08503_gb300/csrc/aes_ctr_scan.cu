@@ -105,8 +105,9 @@ extern "C" aes_status aes_ctr_crypt(const aes_key_schedule* ks, const uint8_t* c
   const KeyWords kw = enc_key_words(*ks, nullptr);
   CtrKernel k = ks->nr == 10 ? ctr_kernel<10> : ks->nr == 12 ? ctr_kernel<12> : ctr_kernel<14>;
   const size_t smem = ttable_smem_bytes(AES_ENCRYPT);
-  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(CTR)");
+  aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k), smem);
+  if (ast != AES_OK) return ast;
+  cudaError_t e;
   const size_t want = (nblocks + 511) / 512;
   const unsigned grid = unsigned(want < size_t(di->sms) ? want : size_t(di->sms));
   k<<<grid, 512, smem, static_cast<cudaStream_t>(cuda_stream)>>>(static_cast<const uint4*>(d_in), static_cast<uint4*>(d_out),

@@ -458,15 +458,17 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
   cudaError_t e;
   if (nb == 0) {  // nothing hashed: the tag is Cipher(J0)
     EmptyFn k0 = ks->nr == 10 ? gcm_empty_kernel<10> : ks->nr == 12 ? gcm_empty_kernel<12> : gcm_empty_kernel<14>;
-    if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k0), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kAesSmem))) != cudaSuccess)
-      return cuda_error(e, "cudaFuncSetAttribute(GCM)");
+    aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k0), kAesSmem);
+    if (ast != AES_OK) return ast;
     k0<<<1, kThreads, kAesSmem, st>>>(kw, ivw[0], ivw[1], ivw[2], d_tag);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM launch");
     return AES_OK;
   }
   GcmFn k = ks->nr == 10 ? gcm_kernel<10, kUnroll> : ks->nr == 12 ? gcm_kernel<12, kUnroll> : gcm_kernel<14, kUnroll>;
-  if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMainSmem))) != cudaSuccess)
-    return cuda_error(e, "cudaFuncSetAttribute(GCM)");
+  {
+    aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k), kMainSmem);
+    if (ast != AES_OK) return ast;
+  }
   // the finished-CTA ticket starts at zero (the last CTA also puts it back)
   if ((e = cudaMemsetAsync(work + kCounter, 0, sizeof(unsigned), st)) != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(GCM ticket)");
   GcmArgs g;

@@ -40,6 +40,13 @@ struct DeviceInfo {
 // a CUDA failure.
 const DeviceInfo* current_device_info();
 
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current device, once per
+// (device, kernel, size): later calls find it in a small cache and skip the driver call, which
+// would otherwise sit on every launch's critical path.
+aes_status ensure_kernel_smem(const void* fn, size_t bytes);
+// Resident CTAs per SM of a kernel on the current device (cached like ensure_kernel_smem).
+aes_status kernel_ctas_per_sm(const void* fn, int threads, size_t smem, int* out);
+
 // ---- key words -------------------------------------------------------------------------
 // Encryption: round key 0 has the IV folded in (C = E(P ^ IV) needs P ^ IV ^ K0).
 KeyWords enc_key_words(const aes_key_schedule& ks, const uint8_t* iv);

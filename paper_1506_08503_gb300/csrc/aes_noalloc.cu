@@ -141,8 +141,10 @@ extern "C" aes_status aes_crypt_batched_noalloc(const aes_key_schedule* schedule
     const size_t smem = ttable_smem_bytes(dir);
     auto k = dir == AES_ENCRYPT ? tt::tt_batched_kernel<AES_ENCRYPT, kThreads, kBlocksPerLane>
                                 : tt::tt_batched_kernel<AES_DECRYPT, kThreads, kBlocksPerLane>;
-    if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
-      return cuda_error(e, "cudaFuncSetAttribute");
+    {
+      aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k), smem);
+      if (ast != AES_OK) return ast;
+    }
     const uint64_t want = (total + kThreads - 1) / kThreads;
     const unsigned grid = unsigned(want < uint64_t(di->sms) ? want : uint64_t(di->sms));
     k<<<grid, kThreads, smem, s>>>(in_base, out_base, bd, dev->keys);

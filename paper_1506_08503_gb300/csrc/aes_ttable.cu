@@ -23,11 +23,9 @@ aes_status launch_ttable(int dir, int nr, const KeyWords& kw, const void* d_in, 
   if (smem > size_t(di->smem_optin))
     return set_error(AES_EINVAL, "device allows %d bytes of shared memory per block, T-tables need %zu",
                      di->smem_optin, smem);
-  // Setting the attribute is idempotent and cheap; doing it on every launch keeps the
-  // code free of per-device caches.
-  cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(T-table kernel)");
+  aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k), smem);
+  if (ast != AES_OK) return ast;
+  cudaError_t e;
   const size_t want = (nblocks + cfg.threads - 1) / cfg.threads;
   const size_t cap = size_t(di->sms) * size_t(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : 1);
   const unsigned grid = unsigned(want < cap ? want : cap);
