@@ -219,7 +219,8 @@ typedef struct aes_batch aes_batch;
 
 /* A reusable batch context bound to `pool`: device descriptor buffers, pinned staging and the
  * cached CUDA graph.  max_msgs is the largest message count a single run may carry
- * (1..2^24).  AES_ENOMEM if its buffers cannot be allocated. */
+ * (1..2^24).  Its launch shape starts at 512-thread CTAs with 1 block per lane per window
+ * (see aes_batch_autotune).  AES_ENOMEM if its buffers cannot be allocated. */
 aes_status aes_batch_create(aes_keypool* pool, size_t max_msgs, aes_batch** out);
 
 /* Runs every message of `msgs` (host array of nmsgs <= max_msgs) reading d_in and writing

@@ -109,7 +109,7 @@ struct aes_batch {
   size_t max_msgs = 0;
   size_t bytes = 0;
   size_t wmax = 0;
-  int threads = 512, bpl = 2;
+  int threads = 512, bpl = 1;  // default shape (the autotuner may change it); measured on the served mix: 1 ~ 2 > 4
   Slot slot[2];
   int next = 0;
   cudaStream_t copy_stream = nullptr;
