@@ -123,10 +123,13 @@ cbc_encrypt_staged(const uint4* in, uint4* out, const uint4* ivs, int iv_stride,
   }
 }
 
+// Decryption, one lane per block in grid-stride order.  The block's message and position in
+// it advance with the stride (its quotient and remainder by the message length come from the
+// host), so no lane divides per block.
 template <int NR>
 __global__ void __launch_bounds__(512, 1)
 cbc_decrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride, uint64_t nmsgs, uint64_t mblocks,
-                   const KeyWords kw) {
+                   const KeyWords kw, uint64_t stride_q, uint64_t stride_r) {
   extern __shared__ __align__(16) uint32_t smem[];
   fill_tables<AES_DECRYPT>(smem);
   __syncthreads();
@@ -134,22 +137,34 @@ cbc_decrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride,
   const uint32_t lc = (threadIdx.x & 31u) * 4u;
   const uint64_t total = nmsgs * mblocks;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < total; g += stride) {
-    const uint64_t msg = g / mblocks, j = g - msg * mblocks;
+  uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  uint64_t msg = g / mblocks, j = g - msg * mblocks;  // once per thread
+  for (; g < total; g += stride) {
     const uint4 c = ld_cached(in + g);
     const uint4 prev = j ? ld_cached(in + g - 1) : ld_cached(ivs + (iv_stride ? msg : 0));
     st_block(out + g, xor4(crypt_block<NR, AES_DECRYPT>(c, kw, sm, lc), prev));
+    msg += stride_q;
+    j += stride_r;
+    if (j >= mblocks) {
+      j -= mblocks;
+      ++msg;
+    }
   }
 }
 
 using CbcKernel = void (*)(const uint4*, uint4*, const uint4*, int, uint64_t, uint64_t, const KeyWords);
+using CbcDecKernel = void (*)(const uint4*, uint4*, const uint4*, int, uint64_t, uint64_t, const KeyWords, uint64_t,
+                              uint64_t);
 
 CbcKernel pick_staged(int nr) {
   return nr == 10 ? cbc_encrypt_staged<10> : nr == 12 ? cbc_encrypt_staged<12> : cbc_encrypt_staged<14>;
 }
 
-CbcKernel pick(int dir, int nr) {
-  if (dir == AES_ENCRYPT) return nr == 10 ? cbc_encrypt_kernel<10> : nr == 12 ? cbc_encrypt_kernel<12> : cbc_encrypt_kernel<14>;
+CbcKernel pick_encrypt(int nr) {
+  return nr == 10 ? cbc_encrypt_kernel<10> : nr == 12 ? cbc_encrypt_kernel<12> : cbc_encrypt_kernel<14>;
+}
+
+CbcDecKernel pick_decrypt(int nr) {
   return nr == 10 ? cbc_decrypt_kernel<10> : nr == 12 ? cbc_decrypt_kernel<12> : cbc_decrypt_kernel<14>;
 }
 
@@ -182,9 +197,10 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   // encryption of enough messages to give every warp of a full GPU 32 of them takes the
   // staged kernel; fewer messages are latency-bound chains, better spread one per lane
   const bool staged = dir == AES_ENCRYPT && nmsgs >= uint64_t(di->sms) * kStagedThreads;
-  CbcKernel k = staged ? pick_staged(ks->nr) : pick(dir, ks->nr);
+  CbcKernel k = dir == AES_DECRYPT ? nullptr : staged ? pick_staged(ks->nr) : pick_encrypt(ks->nr);
+  CbcDecKernel kd = dir == AES_DECRYPT ? pick_decrypt(ks->nr) : nullptr;
   const size_t smem = ttable_smem_bytes(dir) + (staged ? size_t(kStagedThreads / 32) * kTileBytes : 0);
-  aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k), smem);
+  aes_status ast = ensure_kernel_smem(k ? reinterpret_cast<const void*>(k) : reinterpret_cast<const void*>(kd), smem);
   if (ast != AES_OK) return ast;
   cudaError_t e;
   unsigned threads = 512u;
@@ -200,9 +216,16 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   }
   const uint64_t want = (work + threads - 1) / threads;
   const unsigned grid = unsigned(want < uint64_t(di->sms) ? want : uint64_t(di->sms));
-  k<<<grid, threads, smem, static_cast<cudaStream_t>(cuda_stream)>>>(
-      static_cast<const uint4*>(d_in), static_cast<uint4*>(d_out), static_cast<const uint4*>(d_ivs), iv_per_msg,
-      nmsgs, blocks_per_msg, kw);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (kd) {
+    const uint64_t stride = uint64_t(grid) * threads;
+    kd<<<grid, threads, smem, st>>>(static_cast<const uint4*>(d_in), static_cast<uint4*>(d_out),
+                                    static_cast<const uint4*>(d_ivs), iv_per_msg, nmsgs, blocks_per_msg, kw,
+                                    stride / blocks_per_msg, stride % blocks_per_msg);
+  } else {
+    k<<<grid, threads, smem, st>>>(static_cast<const uint4*>(d_in), static_cast<uint4*>(d_out),
+                                   static_cast<const uint4*>(d_ivs), iv_per_msg, nmsgs, blocks_per_msg, kw);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "CBC kernel launch");
   return AES_OK;
 }
