@@ -657,7 +657,8 @@ def run_ours(args):
 
     # ---- the same launches in place (output over input), outside the timed region ------------
     in_place = None
-    if rank == 0:
+    extras = rank == 0 and world == 1  # single-GPU measurements, reported at N = 1 only
+    if extras:
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ip_enc, ip_dec = [], []
         for _ in range(10):
@@ -679,20 +680,20 @@ def run_ours(args):
                     "decrypt_gbs_best": n * 16 / (min(ip_dec) / 1e3) / 1e9, "repetitions": 10}
 
     batched = None
-    if not args.no_batched and rank == 0:
+    if not args.no_batched and extras:
         batched = measure_batched(aes, torch, dev, max(10, min(args.steps, 50)), roofline["enc_gbs"])
 
     followons = None
-    if not args.no_followons and rank == 0:
+    if not args.no_followons and extras:
         followons = measure_followons(aes, torch, dev, x, n, key)
         followons["small_4096_blocks"] = measure_small_latency(aes, torch, dev)
 
     cbc = None
-    if not args.no_cbc and rank == 0:
+    if not args.no_cbc and extras:
         cbc = measure_cbc(aes, torch, dev)
 
     served = None
-    if not args.no_served and rank == 0:
+    if not args.no_served and extras:
         served = measure_served(aes, torch, dev, args.served_requests, roofline["enc_gbs"])
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ---------------------------------------------
