@@ -653,7 +653,11 @@ def run_ours(args):
                 "enc_gbs_median": n * 16 / (statistics.median(enc_ms) / 1e3) / 1e9,
                 "dec_gbs_median": n * 16 / (statistics.median(dec_ms) / 1e3) / 1e9,
                 "enc_gbs_best": n * 16 / (min(enc_ms) / 1e3) / 1e9, "dec_gbs_best": n * 16 / (min(dec_ms) / 1e3) / 1e9,
-                "hbm_term_gbs": 6774.2 / 2}
+                "hbm_term_gbs": 6774.2 / 2,
+                # the T-table design's own ceiling: 160 lookups (5 wavefronts) plus the block's
+                # 16-byte load and store (1/8 wavefront each) through the L1/shared-memory path
+                "lds_path_bound_gbs": sms * SM_MAX_MHZ_NOMINAL * 1e6 / 5.25 * 16 / 1e9}
+    roofline["frac_of_lds_path_bound"] = achieved / roofline["lds_path_bound_gbs"]
 
     # ---- the same launches in place (output over input), outside the timed region ------------
     in_place = None

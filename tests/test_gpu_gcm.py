@@ -128,3 +128,44 @@ def test_gcm_full_size_1gib(aes, orc, cuda):
     assert (host(tag3) == (ej0 ^ s)).all()
     del x
     torch.cuda.empty_cache()
+
+
+def test_gcm_beyond_4gib(aes, orc, cuda):
+    """2^28 + 1027 blocks (just over 4 GiB): positions, counters and GHASH exponents past 2^28
+    blocks and byte offsets past 2^32.  A sparse ciphertext gives a closed-form tag; sampled
+    blocks on both sides of 2^28 are checked against the oracle's cipher of their counters."""
+    import torch
+
+    c = (1 << 28) + 1027
+    rng = np.random.default_rng(12)
+    key, iv = rng.integers(0, 256, 16, dtype=np.uint8), rng.integers(0, 256, 12, dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes())
+    x = torch.zeros(16 * c, dtype=torch.uint8, device="cuda")
+    pos = [0, 77_823, (1 << 28) - 1, 1 << 28, (1 << 28) + 1, c - 1]
+    vals = rng.integers(0, 256, (len(pos), 16), dtype=np.uint8)
+    x.view(-1, 16)[torch.tensor(pos, device="cuda")] = torch.from_numpy(vals).cuda()
+    aad = torch.from_numpy(rng.integers(0, 256, 20, dtype=np.uint8)).cuda()
+    out, tag = aes.gcm(x, ks, iv.tobytes(), aad=aad, dir="decrypt")
+    h = orc.encrypt_blocks(key, np.zeros(16, dtype=np.uint8))
+    ej0 = orc.encrypt_blocks(key, np.concatenate([iv, np.array([0, 0, 0, 1], dtype=np.uint8)]))
+    a_host = aad.cpu().numpy()
+    a_blocks = np.zeros(32, dtype=np.uint8)
+    a_blocks[:20] = a_host
+    m = 2 + c + 1  # AAD blocks, data blocks, length block
+    s = orc.gf128_mul(a_blocks[:16], _power(orc, h, m)) ^ orc.gf128_mul(a_blocks[16:], _power(orc, h, m - 1))
+    for j, v in zip(pos, vals):
+        s ^= orc.gf128_mul(v, _power(orc, h, c - j + 1))
+    lens = np.frombuffer((160).to_bytes(8, "big") + (128 * c).to_bytes(8, "big"), dtype=np.uint8)
+    s ^= orc.gf128_mul(lens, h)
+    assert (tag.cpu().numpy() == (ej0 ^ s)).all()
+    # keystream blocks: out_j = x_j + Cipher(IV || 2 + j)
+    idx = np.array(pos + [12345, (1 << 28) + 700], dtype=np.int64)
+    got = out.view(-1, 16)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    src = x.view(-1, 16)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ctrs = np.zeros((idx.size, 16), dtype=np.uint8)
+    ctrs[:, :12] = iv
+    ctrs[:, 12:] = np.frombuffer(b"".join(int(2 + j).to_bytes(4, "big") for j in idx), dtype=np.uint8).reshape(-1, 4)
+    ksb = orc.encrypt_blocks(key, ctrs.reshape(-1)).reshape(-1, 16)
+    assert (got == (src ^ ksb)).all()
+    del x, out
+    torch.cuda.empty_cache()
