@@ -78,6 +78,9 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     p.add_argument("--nblocks", type=int, default=NBLOCKS, help="blocks per rank (default 2^26 = 1 GiB)")
     p.add_argument("--no-batched", action="store_true", help="skip the 4096-message batched measurement")
+    p.add_argument("--batched-shape", default=None,
+                   help="T,U: run the batched measurement at this CTA size and blocks per lane instead of "
+                        "autotuning (the tuner's timings are meaningless under a profiler)")
     p.add_argument("--no-served", action="store_true", help="skip the served (request server) measurement")
     p.add_argument("--served-requests", type=int, default=10000, help="requests per offered rate")
     p.add_argument("--no-cbc", action="store_true", help="skip the multi-block CBC measurement")
@@ -209,7 +212,7 @@ def read_profile_traffic() -> float | None:
     return None
 
 
-def measure_batched(aes, torch, dev, steps: int, plain_gbs: float) -> dict:
+def measure_batched(aes, torch, dev, steps: int, plain_gbs: float, fixed_shape=None) -> dict:
     """4096 messages, lognormal lengths (median 4 KiB, sigma 1.5), one AES-128 key each (seed 3),
     encrypted in one autotuned persistent launch per step.  Four copies of the 52.6 MB workload
     sit at different places in device memory and the steps cycle through them back to back, so
@@ -227,7 +230,11 @@ def measure_batched(aes, torch, dev, steps: int, plain_gbs: float) -> dict:
         x = torch.from_numpy(np.tile(m.data, copies)).to(dev)
         y = torch.empty_like(x)
         with aes.Batch(pool, len(m.lengths)) as b:
-            shape = b.autotune(msgs, x.data_ptr(), y.data_ptr(), total)
+            if fixed_shape:
+                b.set_shape(*fixed_shape)
+                shape = tuple(fixed_shape)
+            else:
+                shape = b.autotune(msgs, x.data_ptr(), y.data_ptr(), total)
             ptrs = [(x.data_ptr() + k * total, y.data_ptr() + k * total) for k in range(copies)]
             for k in range(2 * copies):
                 b.run(msgs, *ptrs[k % copies], total)
@@ -685,7 +692,8 @@ def run_ours(args):
 
     batched = None
     if not args.no_batched and extras:
-        batched = measure_batched(aes, torch, dev, max(10, min(args.steps, 50)), roofline["enc_gbs"])
+        fixed = tuple(int(v) for v in args.batched_shape.split(",")) if args.batched_shape else None
+        batched = measure_batched(aes, torch, dev, max(10, min(args.steps, 50)), roofline["enc_gbs"], fixed)
 
     followons = None
     if not args.no_followons and extras:
