@@ -139,16 +139,33 @@ cbc_decrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride,
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   uint64_t msg = g / mblocks, j = g - msg * mblocks;  // once per thread
-  for (; g < total; g += stride) {
+  auto advance = [&](uint64_t& m, uint64_t& q) {
+    m += stride_q;
+    q += stride_r;
+    if (q >= mblocks) {
+      q -= mblocks;
+      ++m;
+    }
+  };
+  // two blocks in flight per thread (g and g + stride), as in the independent-block kernel
+  for (; g + stride < total; g += 2 * stride) {
+    uint64_t msg1 = msg, j1 = j;
+    advance(msg1, j1);
+    const uint4 c0 = ld_cached(in + g), c1 = ld_cached(in + g + stride);
+    const uint4 p0 = j ? ld_cached(in + g - 1) : ld_cached(ivs + (iv_stride ? msg : 0));
+    const uint4 p1 = j1 ? ld_cached(in + g + stride - 1) : ld_cached(ivs + (iv_stride ? msg1 : 0));
+    const uint4 d0 = crypt_block<NR, AES_DECRYPT>(c0, kw, sm, lc);
+    const uint4 d1 = crypt_block<NR, AES_DECRYPT>(c1, kw, sm, lc);
+    st_block(out + g, xor4(d0, p0));
+    st_block(out + g + stride, xor4(d1, p1));
+    msg = msg1;
+    j = j1;
+    advance(msg, j);
+  }
+  if (g < total) {
     const uint4 c = ld_cached(in + g);
     const uint4 prev = j ? ld_cached(in + g - 1) : ld_cached(ivs + (iv_stride ? msg : 0));
     st_block(out + g, xor4(crypt_block<NR, AES_DECRYPT>(c, kw, sm, lc), prev));
-    msg += stride_q;
-    j += stride_r;
-    if (j >= mblocks) {
-      j -= mblocks;
-      ++msg;
-    }
   }
 }
 

@@ -39,7 +39,16 @@ ctr_kernel(const uint4* in, uint4* out, size_t nblocks, uint64_t ctr_hi, uint64_
   const char* sm = reinterpret_cast<const char*>(smem);
   const uint32_t lc = (threadIdx.x & 31u) * 4u;
   const size_t stride = size_t(gridDim.x) * blockDim.x;
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nblocks; i += stride) {
+  size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  // two blocks in flight per thread, as in the independent-block kernel
+  for (; i + stride < nblocks; i += 2 * stride) {
+    const uint4 p0 = ld_block(in + i), p1 = ld_block(in + i + stride);
+    const uint4 k0 = crypt_block<NR, AES_ENCRYPT>(counter_block(ctr_hi, ctr_lo, i), kw, sm, lc);
+    const uint4 k1 = crypt_block<NR, AES_ENCRYPT>(counter_block(ctr_hi, ctr_lo, i + stride), kw, sm, lc);
+    st_block(out + i, make_uint4(p0.x ^ k0.x, p0.y ^ k0.y, p0.z ^ k0.z, p0.w ^ k0.w));
+    st_block(out + i + stride, make_uint4(p1.x ^ k1.x, p1.y ^ k1.y, p1.z ^ k1.z, p1.w ^ k1.w));
+  }
+  if (i < nblocks) {
     const uint4 p = ld_block(in + i);
     const uint4 k = crypt_block<NR, AES_ENCRYPT>(counter_block(ctr_hi, ctr_lo, i), kw, sm, lc);
     st_block(out + i, make_uint4(p.x ^ k.x, p.y ^ k.y, p.z ^ k.z, p.w ^ k.w));
