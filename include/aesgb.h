@@ -311,7 +311,8 @@ typedef struct {
 typedef struct {
   uint64_t submitted, completed, failed, queued, inflight, launches;
   uint64_t bytes_completed;
-  double p50_us, p99_us, max_us, mean_us; /* submit-to-completion latency of completed requests */
+  double p50_us, p99_us, max_us, mean_us; /* submit-to-completion latency of the completed requests
+                                            (the most recent 2^22 since the last reset) */
   double gbps;                            /* bytes_completed / (last completion - first submit) */
   double mean_batch;                      /* requests per launch */
   double gbps_from_first_launch;          /* bytes_completed / (last completion - first launch) */

@@ -41,6 +41,7 @@ namespace {
 
 using namespace aesgb;
 using Clock = std::chrono::steady_clock;
+constexpr size_t kLatencyWindow = size_t(1) << 22;  // latencies kept for p50/p99
 
 double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
 
@@ -146,7 +147,10 @@ struct aes_server {
   std::vector<std::thread> issuers;  // one per stream slot
 
   // statistics
+  // latencies of the most recent completions (a ring of kLatencyWindow entries, so a server
+  // that runs for days keeps bounded memory); lat_n counts all recorded since the last reset
   std::vector<double> lat_us;
+  uint64_t lat_n = 0;
   uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, launched_reqs = 0, bytes_done = 0;
   double t_first = 0, t_last = 0, t_first_launch = 0;
 
@@ -197,7 +201,11 @@ void retire(aes_server* s, StreamSlot& sl, double t, int state) {
     if (state == AES_REQ_DONE) {
       s->completed += n;
       s->bytes_done += bytes;
-      s->lat_us.insert(s->lat_us.end(), sl.lat.begin(), sl.lat.end());
+      for (double v : sl.lat) {
+        if (s->lat_us.size() < kLatencyWindow) s->lat_us.push_back(v);
+        else s->lat_us[s->lat_n % kLatencyWindow] = v;
+        ++s->lat_n;
+      }
       if (t > s->t_last) s->t_last = t;
     } else {
       s->failed += n;
@@ -495,7 +503,7 @@ aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_s
   while (ring < cfg->queue_capacity) ring <<= 1;
   try {
     s->ring.reset(new Req[ring]);
-    s->lat_us.reserve(std::min<size_t>(ring, size_t(1) << 22));
+    s->lat_us.reserve(std::min<size_t>(ring, kLatencyWindow));
   } catch (...) {
     aes_server_destroy(s);
     return set_error(AES_ENOMEM, "request ring of %zu entries could not be allocated", ring);
@@ -654,6 +662,7 @@ aes_status aes_server_stats_reset(aes_server* s) {
   if (!s) return set_error(AES_EINVAL, "null server");
   std::lock_guard<std::mutex> lk(s->mu);
   s->lat_us.clear();
+  s->lat_n = 0;
   s->submitted = s->completed = s->failed = s->launches = s->launched_reqs = s->bytes_done = 0;
   s->t_first = s->t_last = s->t_first_launch = 0;
   return AES_OK;
