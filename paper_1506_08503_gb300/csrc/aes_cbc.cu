@@ -66,7 +66,7 @@ cbc_encrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride,
 constexpr int kStage = 8;
 constexpr uint32_t kRows = 32;
 constexpr uint32_t kTileBytes = kRows * (kStage + 1) * 16u;  // per warp
-constexpr uint32_t kStagedThreads = 512;
+constexpr uint32_t kStagedThreads = 640;
 constexpr int kPer = int(kRows) * kStage / 32;  // tile elements per lane
 
 template <int NR>
@@ -223,6 +223,7 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   unsigned threads = 512u;
   uint64_t work = uint64_t(nmsgs) * blocks_per_msg;
   if (staged) {
+    threads = kStagedThreads;  // the kernel's warp-to-group map assumes this CTA size
     work = (nmsgs + kRows - 1) / kRows * 32;  // kRows messages per warp
   } else if (dir == AES_ENCRYPT) {
     // a lane per message: with few messages, spread the chains over all SMs (smaller CTAs)

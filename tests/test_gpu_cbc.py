@@ -114,7 +114,7 @@ def test_staged_encrypt_ragged(aes_lib_ready, orc, m):
     that leaves the last warp's group partial, and lengths that leave the last stage partial."""
     import torch
 
-    n = 152 * 512 + 37
+    n = 160_037  # above the staged kernel's threshold (one group of 32 per warp of a full GPU)
     g = torch.Generator(device="cuda").manual_seed(84 + m)
     x = torch.randint(0, 256, (n, 16 * m), dtype=torch.uint8, device="cuda", generator=g)
     ivs = torch.randint(0, 256, (n, 16), dtype=torch.uint8, device="cuda", generator=g)
