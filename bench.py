@@ -78,6 +78,9 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     p.add_argument("--nblocks", type=int, default=NBLOCKS, help="blocks per rank (default 2^26 = 1 GiB)")
     p.add_argument("--no-batched", action="store_true", help="skip the 4096-message batched measurement")
+    p.add_argument("--tt-shape", default=None,
+                   help="T,U: set the AUTO kernel to the T-table kernel with this CTA size and blocks per "
+                        "thread instead of running the launch tuner (for profiling)")
     p.add_argument("--batched-shape", default=None,
                    help="T,U: run the batched measurement at this CTA size and blocks per lane instead of "
                         "autotuning (the tuner's timings are meaningless under a profiler)")
@@ -197,19 +200,20 @@ def run_reference(args):
     return 0
 
 
-def read_profile_traffic() -> float | None:
-    """DRAM bytes per launch of the encryption kernel, from the committed ncu summary (the
-    line `traffic_bytes_per_launch: <n>` of the committed ncu summary of the encryption kernel)."""
+def read_profile_traffic() -> tuple[float | None, tuple[int, int] | None]:
+    """DRAM bytes per launch of the encryption kernel and the (threads, blocks per thread) shape
+    they were taken on, from the committed ncu summary (its lines `traffic_bytes_per_launch: <n>`
+    and `profiled_shape: <threads>,<blocks per thread>`)."""
     f = ROOT / "profiles" / "tt_kernel_aes128_256MiB.md"
-    if not f.exists():
-        return None
-    for line in f.read_text().splitlines():
-        if line.startswith("traffic_bytes_per_launch:"):
-            try:
-                return float(line.split(":", 1)[1].strip().split()[0])
-            except ValueError:
-                return None
-    return None
+    traffic, shape = None, None
+    if f.exists():
+        for line in f.read_text().splitlines():
+            if line.startswith("traffic_bytes_per_launch:"):
+                traffic = float(line.split(":", 1)[1].split()[0])
+            if line.startswith("profiled_shape:"):
+                t, u = line.split(":", 1)[1].split()[0].split(",")
+                shape = (int(t), int(u))
+    return traffic, shape
 
 
 def measure_batched(aes, torch, dev, steps: int, plain_gbs: float, fixed_shape=None) -> dict:
@@ -573,7 +577,13 @@ def run_ours(args):
 
     # the launch tuner picks the AUTO kernel (T-table shapes and the bitsliced kernel), untimed
     tuned = None
-    if args.kernel == "auto":
+    if args.kernel == "auto" and args.tt_shape:
+        t_, u_ = (int(v) for v in args.tt_shape.split(","))
+        for d in ("encrypt", "decrypt"):
+            aes.aes_set_auto_choice(d, 10, "ttable", t_, u_)
+        tuned = {d: {"impl": "ttable", "threads": t_, "blocks_per_thread": u_, "set_by": "--tt-shape"}
+                 for d in ("encrypt", "decrypt")}
+    elif args.kernel == "auto":
         tuned = {d: aes.aes_autotune_blocks(ks0, xp, cp if d == "encrypt" else pp, n, d) for d in ("encrypt", "decrypt")}
     for _ in range(max(args.warmup, 3)):
         step()
@@ -646,11 +656,12 @@ def run_ours(args):
     dom_ms = max(enc_avg, dec_avg)
     dom = "encrypt" if enc_avg >= dec_avg else "decrypt"
     achieved = n * 16 / (dom_ms / 1e3) / 1e9
-    # the committed ncu traffic figure is for the 512-thread, two-blocks-per-thread T-table shape
+    # the committed ncu traffic figure holds only for the shape it was taken on
     shape = tuned[dom] if tuned else {"impl": args.kernel if args.kernel != "auto" else "ttable", "threads": 512,
                                       "blocks_per_thread": 2}
-    profiled_shape = shape["impl"] == "ttable" and shape["threads"] == 512 and shape["blocks_per_thread"] == 2
-    traffic = read_profile_traffic() if profiled_shape and n == NBLOCKS else None
+    prof_traffic, prof_shape = read_profile_traffic()
+    same_shape = shape["impl"] == "ttable" and (shape["threads"], shape["blocks_per_thread"]) == prof_shape
+    traffic = prof_traffic if same_shape and n == NBLOCKS else None
     kname = (f"tt_kernel<10,{dom},{shape['threads']},{shape['blocks_per_thread']}>" if shape["impl"] == "ttable"
              else f"bs_kernel<10,{dom}>")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

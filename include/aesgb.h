@@ -97,7 +97,8 @@ aes_status aes_crypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, const
 /* Tunes AES_IMPL_AUTO for the current device, `dir` and ks->nr: times every compiled
  * candidate on d_in -> d_out (nblocks blocks, device, 16-byte aligned; d_out is overwritten):
  * the T-table kernel with CTAs of 512 threads and 1, 2 or 4 blocks in flight per thread, 256
- * threads and 4, 1024 threads and 1 or 2, and the bitsliced kernel (32 blocks per thread).
+ * threads and 4, 768 threads and 2, 1024 threads and 1 or 2, and the bitsliced kernel (32
+ * blocks per thread).
  * The fastest serves later AES_IMPL_AUTO calls in this process.  If cache_path is not NULL
  * the choice is also recorded in that JSON file, keyed by device name, direction, round count
  * and floor(log2(nblocks)); an existing entry is used without timing.  Writes the choice to
@@ -105,6 +106,11 @@ aes_status aes_crypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, const
  * Synchronous: it waits for its timing launches.  nblocks = 0 is AES_EINVAL. */
 aes_status aes_autotune_blocks(const aes_key_schedule* ks, const void* d_in, void* d_out, size_t nblocks, int dir,
                                const char* cache_path, int* impl, int* threads, int* unroll, void* cuda_stream);
+
+/* Sets the AES_IMPL_AUTO choice for the current device, `dir` and round count `nr` (10, 12,
+ * 14) directly, without timing: impl AES_IMPL_TTABLE with one of the (threads, unroll) pairs
+ * aes_autotune_blocks tries, or AES_IMPL_BITSLICE with (128, 32).  AES_EINVAL otherwise. */
+aes_status aes_set_auto_choice(int dir, int nr, int impl, int threads, int unroll);
 
 /* The paper's CBC mode over whole messages (Section II; App. A1 encryption, App. A4
  * decryption).  d_in and d_out (device) hold an nmsgs x (16 * blocks_per_msg) byte matrix, one

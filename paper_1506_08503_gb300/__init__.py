@@ -112,6 +112,7 @@ _SIGS: dict[str, tuple] = {
     "aes_scan_equal": (_I, [_VP, _SZ, _U8P, _VP, _SZ, _VP, _VP]),
     "aes_autotune_blocks": (_I, [_KSP, _VP, _VP, _SZ, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I),
                                  ctypes.POINTER(_I), _VP]),
+    "aes_set_auto_choice": (_I, [_I, _I, _I, _I, _I]),
     "aes_gcm_workspace_bytes": (_SZ, []),
     "aes_gcm_crypt": (_I, [_KSP, _U8P, _SZ, _VP, _SZ, _VP, _VP, _SZ, _I, _VP, _VP, _SZ, _VP]),
     "aes_crypt_batched_noalloc": (_I, [_KSP, ctypes.c_uint32, _VP, _SZ, _VP, _VP, _SZ, _VP]),
@@ -284,6 +285,12 @@ def aes_autotune_blocks(ks: aes_key_schedule, d_in: int, d_out: int, nblocks: in
                                      ctypes.byref(t), ctypes.byref(u), _stream_ptr(stream)))
     return {"impl": {AES_IMPL_TTABLE: "ttable", AES_IMPL_BITSLICE: "bitslice"}.get(i.value, i.value),
             "threads": t.value, "blocks_per_thread": u.value}
+
+
+def aes_set_auto_choice(dir, nr: int, impl, threads: int, blocks_per_thread: int) -> None:
+    """Sets the AES_IMPL_AUTO kernel for this device, direction and round count directly."""
+    code = {"ttable": AES_IMPL_TTABLE, "bitslice": AES_IMPL_BITSLICE}.get(impl, impl)
+    _check(lib().aes_set_auto_choice(_dir(dir), nr, int(code), threads, blocks_per_thread))
 
 
 def aes_gcm_workspace_bytes() -> int:

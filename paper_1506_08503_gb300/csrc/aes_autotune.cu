@@ -21,6 +21,7 @@ struct Candidate {
 // every compiled T-table shape (see tt::select_config) and the bitsliced kernel
 constexpr Candidate kCandidates[] = {{AES_IMPL_TTABLE, 512, 2},  {AES_IMPL_TTABLE, 512, 1},  {AES_IMPL_TTABLE, 512, 4},
                                      {AES_IMPL_TTABLE, 256, 4},  {AES_IMPL_TTABLE, 1024, 1}, {AES_IMPL_TTABLE, 1024, 2},
+                                     {AES_IMPL_TTABLE, 768, 2},
                                      {AES_IMPL_BITSLICE, 128, 32}};
 constexpr int kDevices = 64;
 
@@ -179,5 +180,22 @@ extern "C" aes_status aes_autotune_blocks(const aes_key_schedule* ks, const void
   if (impl) *impl = best.impl;
   if (threads) *threads = best.threads;
   if (unroll) *unroll = best.unroll;
+  return AES_OK;
+}
+
+extern "C" aes_status aes_set_auto_choice(int dir, int nr, int impl, int threads, int unroll) {
+  clear_error();
+  if (dir != AES_ENCRYPT && dir != AES_DECRYPT) return set_error(AES_EINVAL, "dir must be AES_ENCRYPT or AES_DECRYPT");
+  if (nr != 10 && nr != 12 && nr != 14) return set_error(AES_EINVAL, "nr must be 10, 12 or 14");
+  const Candidate c{impl, threads, unroll};
+  if (!valid(c)) return set_error(AES_EINVAL, "(impl %d, %d threads, %d per thread) is not a compiled candidate", impl, threads, unroll);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kDevices) return set_error(AES_ECUDA, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  Tuned& t = g_tuned[dev][dir == AES_DECRYPT][(nr - 10) / 2];
+  t.set = true;
+  t.c = c;
   return AES_OK;
 }

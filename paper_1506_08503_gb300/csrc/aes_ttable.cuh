@@ -176,6 +176,7 @@ TTKernelFn select_config(int threads, int unroll) {
   if (threads == 512 && unroll == 1) return tt_kernel<NR, DIR, 512, 1>;
   if (threads == 512 && unroll == 2) return tt_kernel<NR, DIR, 512, 2>;
   if (threads == 512 && unroll == 4) return tt_kernel<NR, DIR, 512, 4>;
+  if (threads == 768 && unroll == 2) return tt_kernel<NR, DIR, 768, 2>;
   if (threads == 1024 && unroll == 1) return tt_kernel<NR, DIR, 1024, 1>;
   if (threads == 1024 && unroll == 2) return tt_kernel<NR, DIR, 1024, 2>;
   return nullptr;

@@ -148,3 +148,11 @@ def test_autotune_argument_checks_before_any_cuda_call(aes):
     assert lib.aes_autotune_blocks(kp, base + 8, base + 4096, 4, 0, None, None, None, None, None) == aes.AES_EINVAL
     assert lib.aes_autotune_blocks(kp, base, base + 16, 4, 0, None, None, None, None, None) == aes.AES_EINVAL
     assert lib.aes_autotune_blocks(None, base, base + 4096, 4, 0, None, None, None, None, None) == aes.AES_EINVAL
+
+
+def test_set_auto_choice_validates_before_any_cuda_call(aes):
+    lib = aes.lib()
+    assert lib.aes_set_auto_choice(2, 10, aes.AES_IMPL_TTABLE, 512, 2) == aes.AES_EINVAL  # bad dir
+    assert lib.aes_set_auto_choice(0, 11, aes.AES_IMPL_TTABLE, 512, 2) == aes.AES_EINVAL  # bad nr
+    assert lib.aes_set_auto_choice(0, 10, aes.AES_IMPL_TTABLE, 500, 2) == aes.AES_EINVAL  # not compiled
+    assert lib.aes_set_auto_choice(0, 10, 7, 512, 2) == aes.AES_EINVAL

@@ -40,3 +40,18 @@ def test_autotune_then_auto_matches(aes, orc, cuda, tmp_path, key_bits):
         assert (sample == want).all()
     entries = json.loads(cache.read_text())
     assert len(entries) == 2 and all("us" in v for v in entries.values())
+
+
+def test_set_auto_choice_then_auto_matches(aes, cuda):
+    import torch
+
+    w = workloads.plain(92, 300_007)
+    ks = aes.aes_key_expand(w.key.tobytes())
+    x = torch.from_numpy(w.data).cuda()
+    ref = aes.crypt(x, ks, "encrypt", impl="ttable")
+    for threads, u in ((768, 2), (256, 4), (512, 1)):
+        aes.aes_set_auto_choice("encrypt", 10, "ttable", threads, u)
+        assert torch.equal(aes.crypt(x, ks, "encrypt"), ref)
+    aes.aes_set_auto_choice("encrypt", 10, "bitslice", 128, 32)
+    assert torch.equal(aes.crypt(x, ks, "encrypt"), ref)
+    aes.aes_set_auto_choice("encrypt", 10, "ttable", 512, 2)
