@@ -11,6 +11,7 @@
 #include <string>
 
 #include "aes_internal.cuh"
+#include "aesgb_testing.h"
 
 namespace aesgb {
 namespace {
@@ -198,4 +199,21 @@ extern "C" aes_status aes_set_auto_choice(int dir, int nr, int impl, int threads
   t.set = true;
   t.c = c;
   return AES_OK;
+}
+
+extern "C" int aes_testing_tune_cache_store(const char* path, const char* sig, int impl, int threads, int unroll,
+                                            double us) {
+  if (!path || !sig) return -1;
+  cache_store(path, read_file(path), sig, Candidate{impl, threads, unroll}, us);
+  return 0;
+}
+
+extern "C" int aes_testing_tune_cache_lookup(const char* path, const char* sig, int* impl, int* threads, int* unroll) {
+  if (!path || !sig || !impl || !threads || !unroll) return -1;
+  Candidate c{};
+  if (!cache_lookup(read_file(path), sig, &c)) return 0;
+  *impl = c.impl;
+  *threads = c.threads;
+  *unroll = c.unroll;
+  return 1;
 }

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "aes_internal.cuh"
+#include "aesgb_testing.h"
 
 namespace {
 
@@ -497,3 +498,21 @@ aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsg
 }
 
 }  // extern "C"
+
+extern "C" int aes_testing_weighted_slices(const uint64_t* nblocks, const int8_t* rounds, size_t n, uint64_t nw,
+                                           uint64_t* gb, uint32_t* msg) {
+  if (!nblocks || !rounds || !gb || !msg || n == 0 || n > (size_t(1) << 20) || nw == 0) return -1;
+  std::vector<BatchMsg> m(n);
+  std::vector<uint64_t> start(n + 1);
+  uint64_t total = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if (nblocks[i] == 0 || (rounds[i] != 10 && rounds[i] != 12 && rounds[i] != 14)) return -1;
+    m[i] = BatchMsg{uint32_t(i), 0u, 0, 0, nblocks[i]};
+    start[i] = total;
+    total += nblocks[i];
+  }
+  start[n] = total;
+  const uint64_t W = work_of(m.data(), n, rounds);
+  weighted_slices(m.data(), start.data(), n, rounds, W, nw, gb, msg);
+  return 0;
+}

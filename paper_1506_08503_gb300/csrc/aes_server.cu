@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "aes_internal.cuh"
+#include "aesgb_testing.h"
 
 namespace {
 
@@ -669,3 +670,32 @@ aes_status aes_server_stats_reset(aes_server* s) {
 }
 
 }  // extern "C"
+
+extern "C" int aes_testing_arena(size_t size, const int64_t* ops, size_t nops, int64_t* results) {
+  if (!ops || !results) return -1;
+  Arena a(size);
+  std::vector<std::pair<size_t, size_t>> made(nops, {0, 0});  // (offset, bytes) of allocation i
+  std::vector<bool> live(nops, false), freed(nops, false);
+  for (size_t i = 0; i < nops; ++i) {
+    if (ops[i] > 0) {
+      size_t off = 0;
+      if (a.alloc(size_t(ops[i]), &off)) {
+        made[i] = {off, size_t(ops[i])};
+        live[i] = true;
+        results[i] = int64_t(off);
+      } else {
+        results[i] = -1;
+      }
+    } else if (ops[i] < 0) {
+      const uint64_t j = uint64_t(-(ops[i] + 1));
+      if (j >= i || ops[j] <= 0 || freed[j]) return -1;  // not an earlier allocation, or freed twice
+      freed[j] = true;
+      if (live[j]) a.release(made[j].first, made[j].second);  // a failed allocation frees nothing
+      live[j] = false;
+      results[i] = 0;
+    } else {
+      return -1;
+    }
+  }
+  return 0;
+}
