@@ -301,6 +301,20 @@ def measure_cbc(aes, torch, dev) -> dict:
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / 5
             entry[d + "_gbs"] = n * m * 16 / (ms / 1e3) / 1e9
+        if n * m >= 1 << 20:
+            # the independent-block kernel on the same bytes (ECB, same key): what the chain
+            # and the previous-block read cost
+            xf, yf = x.view(-1), y.view(-1)
+            for d, fn in (("encrypt", aes.encrypt), ("decrypt", aes.decrypt)):
+                for _ in range(2):
+                    fn(xf, ks, out=yf)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(5):
+                    fn(xf, ks, out=yf)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                entry["ecb_same_bytes_" + d + "_gbs"] = n * m * 16 / (e0.elapsed_time(e1) / 5 / 1e3) / 1e9
         torch.cuda.synchronize()
         if not torch.equal(z, x):
             raise RuntimeError("CBC round trip failed")

@@ -66,11 +66,11 @@ cbc_encrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride,
 constexpr int kStage = 8;
 constexpr uint32_t kRows = 32;
 constexpr uint32_t kTileBytes = kRows * (kStage + 1) * 16u;  // per warp
-constexpr uint32_t kStagedThreads = 640;
+constexpr uint32_t kStagedThreads = 640;  // the largest CTA whose tiles fit beside the tables
 constexpr int kPer = int(kRows) * kStage / 32;  // tile elements per lane
 
-template <int NR>
-__global__ void __launch_bounds__(kStagedThreads, 1)
+template <int NR, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
 cbc_encrypt_staged(const uint4* in, uint4* out, const uint4* ivs, int iv_stride, uint64_t nmsgs, uint64_t mblocks,
                    const KeyWords kw) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -81,8 +81,8 @@ cbc_encrypt_staged(const uint4* in, uint4* out, const uint4* ivs, int iv_stride,
   const uint32_t lc = lane * 4u;
   uint4* tile = reinterpret_cast<uint4*>(reinterpret_cast<char*>(smem) + 2u * kRegion + warp * kTileBytes);
   const uint64_t ngroups = (nmsgs + kRows - 1) / kRows;
-  const uint64_t nw = uint64_t(gridDim.x) * (kStagedThreads / 32);
-  for (uint64_t grp = uint64_t(blockIdx.x) * (kStagedThreads / 32) + warp; grp < ngroups; grp += nw) {
+  const uint64_t nw = uint64_t(gridDim.x) * (THREADS / 32);
+  for (uint64_t grp = uint64_t(blockIdx.x) * (THREADS / 32) + warp; grp < ngroups; grp += nw) {
     const uint64_t m0 = grp * kRows;
     const uint32_t rows = uint32_t(nmsgs - m0 < kRows ? nmsgs - m0 : kRows);
     uint4 chain = lane < rows ? ld_cached(ivs + (iv_stride ? m0 + lane : 0)) : make_uint4(0u, 0u, 0u, 0u);
@@ -173,8 +173,33 @@ using CbcKernel = void (*)(const uint4*, uint4*, const uint4*, int, uint64_t, ui
 using CbcDecKernel = void (*)(const uint4*, uint4*, const uint4*, int, uint64_t, uint64_t, const KeyWords, uint64_t,
                               uint64_t);
 
-CbcKernel pick_staged(int nr) {
-  return nr == 10 ? cbc_encrypt_staged<10> : nr == 12 ? cbc_encrypt_staged<12> : cbc_encrypt_staged<14>;
+template <int THREADS>
+CbcKernel pick_staged_nr(int nr) {
+  return nr == 10 ? cbc_encrypt_staged<10, THREADS>
+                  : nr == 12 ? cbc_encrypt_staged<12, THREADS> : cbc_encrypt_staged<14, THREADS>;
+}
+
+// CTA size of the staged kernel.  Its warps (one CTA per SM) take the 32-message groups in
+// waves, and every chain of a group is as long as the others, so the last wave, if partly
+// filled, costs a whole wave.  Of 16, 18 and 20 warps per CTA the size with the fewest waves
+// wins, the smaller one among equals (fewer warps finish a wave no later).  2^18 messages on
+// 152 SMs: 16 warps take 4 waves, 18 warps 3 (all but full), 20 warps 3 (the last 69 % full).
+unsigned staged_threads(uint64_t ngroups, int sms) {
+  unsigned best = kStagedThreads;
+  uint64_t best_waves = UINT64_MAX;
+  for (unsigned t = 512; t <= kStagedThreads; t += 64) {
+    const uint64_t per_wave = uint64_t(sms) * (t / 32);
+    const uint64_t waves = (ngroups + per_wave - 1) / per_wave;
+    if (waves < best_waves) {
+      best_waves = waves;
+      best = t;
+    }
+  }
+  return best;
+}
+
+CbcKernel pick_staged(int nr, unsigned threads) {
+  return threads == 512 ? pick_staged_nr<512>(nr) : threads == 576 ? pick_staged_nr<576>(nr) : pick_staged_nr<640>(nr);
 }
 
 CbcKernel pick_encrypt(int nr) {
@@ -214,16 +239,17 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   // encryption of enough messages to give every warp of a full GPU 32 of them takes the
   // staged kernel; fewer messages are latency-bound chains, better spread one per lane
   const bool staged = dir == AES_ENCRYPT && nmsgs >= uint64_t(di->sms) * kStagedThreads;
-  CbcKernel k = dir == AES_DECRYPT ? nullptr : staged ? pick_staged(ks->nr) : pick_encrypt(ks->nr);
+  const unsigned staged_cta = staged ? staged_threads((nmsgs + kRows - 1) / kRows, di->sms) : 0u;
+  CbcKernel k = dir == AES_DECRYPT ? nullptr : staged ? pick_staged(ks->nr, staged_cta) : pick_encrypt(ks->nr);
   CbcDecKernel kd = dir == AES_DECRYPT ? pick_decrypt(ks->nr) : nullptr;
-  const size_t smem = ttable_smem_bytes(dir) + (staged ? size_t(kStagedThreads / 32) * kTileBytes : 0);
+  const size_t smem = ttable_smem_bytes(dir) + (staged ? size_t(staged_cta / 32) * kTileBytes : 0);
   aes_status ast = ensure_kernel_smem(k ? reinterpret_cast<const void*>(k) : reinterpret_cast<const void*>(kd), smem);
   if (ast != AES_OK) return ast;
   cudaError_t e;
   unsigned threads = 512u;
   uint64_t work = uint64_t(nmsgs) * blocks_per_msg;
   if (staged) {
-    threads = kStagedThreads;  // the kernel's warp-to-group map assumes this CTA size
+    threads = staged_cta;  // the kernel instance's warp-to-group map assumes this CTA size
     work = (nmsgs + kRows - 1) / kRows * 32;  // kRows messages per warp
   } else if (dir == AES_ENCRYPT) {
     // a lane per message: with few messages, spread the chains over all SMs (smaller CTAs)

@@ -132,3 +132,27 @@ def test_staged_encrypt_ragged(aes_lib_ready, orc, m):
     torch.cuda.synchronize()
     assert torch.equal(y, ct)
     assert torch.equal(aes.cbc(ct, ks, ivs, "decrypt"), x)
+
+
+@pytest.mark.parametrize("n", [97_280, 97_307, 160_037])
+def test_staged_encrypt_each_cta_size(aes_lib_ready, orc, n):
+    """The staged kernel's CTA size follows the number of 32-message groups (the fewest waves
+    over the SMs).  On a 152-SM GPU these counts take 20, 16 and 18 warps per CTA: 3040 groups
+    (one full wave of 20 warps), 3041 groups (two waves at every size, so the smallest), and
+    5002 groups (two waves of 18 or 20 warps).  AES-192 and one IV for all messages."""
+    import torch
+
+    m = 5
+    g = torch.Generator(device="cuda").manual_seed(86)
+    x = torch.randint(0, 256, (n, 16 * m), dtype=torch.uint8, device="cuda", generator=g)
+    iv = torch.randint(0, 256, (16,), dtype=torch.uint8, device="cuda", generator=g)
+    key = (np.arange(24, dtype=np.uint8) * 7 + 3).astype(np.uint8)
+    ks = aes.aes_key_expand(key.tobytes(), 192)
+    ct = aes.cbc(x, ks, iv, "encrypt")
+    rows = np.unique(np.concatenate([np.arange(0, 33), np.arange(n - 33, n),
+                                     np.random.default_rng(87).integers(0, n, 150)]))
+    tr = torch.from_numpy(rows).cuda()
+    p, c, v = x[tr].cpu().numpy(), ct[tr].cpu().numpy(), iv.cpu().numpy()
+    for k in range(rows.size):
+        assert (c[k] == orc.cbc_encrypt(key, v, p[k])).all(), rows[k]
+    assert torch.equal(aes.cbc(ct, ks, iv, "decrypt"), x)
