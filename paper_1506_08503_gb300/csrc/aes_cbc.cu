@@ -126,8 +126,10 @@ cbc_encrypt_staged(const uint4* in, uint4* out, const uint4* ivs, int iv_stride,
 // Decryption, one lane per block in grid-stride order.  The block's message and position in
 // it advance with the stride (its quotient and remainder by the message length come from the
 // host), so no lane divides per block.
+constexpr unsigned kDecThreads = 768;  // 24 warps per SM, as in the tuned independent-block kernel
+
 template <int NR>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(kDecThreads, 1)
 cbc_decrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride, uint64_t nmsgs, uint64_t mblocks,
                    const KeyWords kw, uint64_t stride_q, uint64_t stride_r) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -246,7 +248,7 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   aes_status ast = ensure_kernel_smem(k ? reinterpret_cast<const void*>(k) : reinterpret_cast<const void*>(kd), smem);
   if (ast != AES_OK) return ast;
   cudaError_t e;
-  unsigned threads = 512u;
+  unsigned threads = dir == AES_DECRYPT ? kDecThreads : 512u;
   uint64_t work = uint64_t(nmsgs) * blocks_per_msg;
   if (staged) {
     threads = staged_cta;  // the kernel instance's warp-to-group map assumes this CTA size

@@ -30,8 +30,12 @@ __device__ __forceinline__ uint4 counter_block(uint64_t hi, uint64_t lo, uint64_
   return make_uint4(bswap32(uint32_t(h >> 32)), bswap32(uint32_t(h)), bswap32(uint32_t(l >> 32)), bswap32(uint32_t(l)));
 }
 
+// 24 warps per SM, as in the tuned independent-block kernel (the 128 KiB of tables allow one
+// CTA per SM, so the CTA takes the warps)
+constexpr unsigned kCtrThreads = 768;
+
 template <int NR>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(kCtrThreads, 1)
 ctr_kernel(const uint4* in, uint4* out, size_t nblocks, uint64_t ctr_hi, uint64_t ctr_lo, const KeyWords kw) {
   extern __shared__ __align__(16) uint32_t smem[];
   fill_tables<AES_ENCRYPT>(smem);
@@ -117,9 +121,9 @@ extern "C" aes_status aes_ctr_crypt(const aes_key_schedule* ks, const uint8_t* c
   aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k), smem);
   if (ast != AES_OK) return ast;
   cudaError_t e;
-  const size_t want = (nblocks + 511) / 512;
+  const size_t want = (nblocks + kCtrThreads - 1) / kCtrThreads;
   const unsigned grid = unsigned(want < size_t(di->sms) ? want : size_t(di->sms));
-  k<<<grid, 512, smem, static_cast<cudaStream_t>(cuda_stream)>>>(static_cast<const uint4*>(d_in), static_cast<uint4*>(d_out),
+  k<<<grid, kCtrThreads, smem, static_cast<cudaStream_t>(cuda_stream)>>>(static_cast<const uint4*>(d_in), static_cast<uint4*>(d_out),
                                                                  nblocks, hi, lo, kw);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "CTR kernel launch");
   return AES_OK;
