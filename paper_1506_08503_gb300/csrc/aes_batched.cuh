@@ -36,6 +36,10 @@ __device__ __forceinline__ uint32_t find_msg(const uint64_t* start, uint32_t nms
   return lo;
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" :: "l"(p));
+}
+
 __device__ __forceinline__ void open_msg(Cursor& c, const BatchDir& bd, uint32_t m) {
   c.m = m;
   c.start = ldg64(bd.start + m);
@@ -90,7 +94,8 @@ __device__ __forceinline__ uint4 crypt_rt(uint4 v, const uint32_t (&kw)[kMaxRoun
 // whole warp (uniform registers and branches), and each lane enciphers U independent blocks.
 // A window cut short by a message end leaves lanes idle; over lognormal lengths (median 4 KiB)
 // that costs a few percent, less than per-lane keys at the boundaries would.  The next window
-// of the same message is prefetched into L2 while the current one is enciphered.  The host
+// of the same message is prefetched into L2 while the current one is enciphered, and during
+// a message's last window the next message's key rows (L1) and first window (L2).  The host
 // gives every warp the message holding its first block (warp_msg), so no warp searches.
 // (Measured alternatives that were slower: the next window loaded into registers one window
 // ahead; the first window issued before the table fill; a separate loop for whole windows,
@@ -151,6 +156,24 @@ __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base
     for (int u = 0; u < U; ++u) {
       const uint64_t i = kWin + u * 32u + lane;
       if (gb + i < nend) prefetch_l2(src + i);
+    }
+    if (wend == c.end && wend < hi) {
+      // the message's last window, and the slice goes on into the next message: the next
+      // key's rows go to L1 and the next message's first window to L2 while this window is
+      // enciphered, so the switch does not wait on either (the next descriptor shares this
+      // one's cache line three times in four)
+      const BatchMsg* nm = bd.msgs + c.m + 1;
+      const uint32_t nkey = __ldg(&nm->key_idx);
+      const uint64_t nsrc = ldg64(&nm->src_block), nlen = ldg64(&nm->nblocks);
+      const PoolEntry* e = pool + nkey;
+      const char* kp = reinterpret_cast<const char*>(DIR == AES_ENCRYPT ? &e->enc[0][0] : &e->dec[0][0]);
+      if (lane <= uint32_t(kMaxRounds)) prefetch_l1(kp + lane * 16u);
+      const uint4* nsp = reinterpret_cast<const uint4*>(in_base + nsrc * 16u);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t i = u * 32u + lane;
+        if (i < nlen) prefetch_l2(nsp + i);
+      }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) v[u] = crypt_rt<DIR>(v[u], kw, kl, nr, sm, lc);
