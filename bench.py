@@ -435,13 +435,15 @@ def measure_followons(aes, torch, dev, x, n: int, key: bytes) -> dict:
 def measure_served(aes, torch, dev, nreq: int, plain_gbs: float) -> dict:
     """The request server under Poisson arrivals (seed 4): 50/50 encrypt/decrypt, sizes
     lognormal (median 4 KiB, sigma 1.5) in [64 B, 64 MiB], keys from a resident pool of 1024
-    (512 AES-128, 512 AES-256), payloads resident in device memory.  Offered rates 1k, 10k
-    and 100k requests/s, then a closed loop (everything submitted at once) for saturation."""
+    (512 AES-128, 512 AES-256), payloads resident in device memory.  Offered rates 1k, 3k,
+    10k, 30k and 100k requests/s (nreq requests each, 10 * nreq at 100k/s: one to ten seconds
+    of arrivals per rate), then a closed loop (everything submitted at once) for saturation."""
     import time as _t
 
     out = {"workload": "Poisson arrivals, 50/50 enc/dec, lognormal(median 4 KiB, sigma 1.5) in [64 B, 64 MiB], "
                        "1024-key pool (half AES-128, half AES-256), device-resident payloads, seed 4",
-           "requests_per_rate": nreq, "closed_loop_requests": 20 * nreq, "rates": []}
+           "requests_per_rate": {"1k-30k req/s": nreq, "100k req/s": 10 * nreq}, "closed_loop_requests": 20 * nreq,
+           "rates": []}
     w0 = workloads.served_requests(4, 1, 1.0)
     pool = aes.KeyPool(len(w0.pool_keys))
     pool.load_keys(0, np.stack(w0.pool_keys[:512]), 128)
@@ -449,8 +451,9 @@ def measure_served(aes, torch, dev, nreq: int, plain_gbs: float) -> dict:
     srv = aes.Server(pool, hbm_budget=1 << 30, max_inflight=1 << 20, nstreams=4, max_batch=8192,
                      queue_capacity=1 << 18)
     try:
-        for rate in (1000.0, 10000.0, 100000.0, None):
-            w = workloads.served_requests(4, nreq if rate else 20 * nreq, rate or 1e9)
+        for rate in (1000.0, 3000.0, 10000.0, 30000.0, 100000.0, None):
+            count = 20 * nreq if rate is None else 10 * nreq if rate >= 1e5 else nreq
+            w = workloads.served_requests(4, count, rate or 1e9)
             offs = np.concatenate([[0], np.cumsum(w.lengths)[:-1]]).astype(np.int64)
             total = int(w.lengths.sum())
             src = torch.randint(0, 256, (total,), dtype=torch.uint8, device=dev)

@@ -225,8 +225,9 @@ typedef struct aes_batch aes_batch;
 
 /* A reusable batch context bound to `pool`: device descriptor buffers, pinned staging and the
  * cached CUDA graph.  max_msgs is the largest message count a single run may carry
- * (1..2^24).  Its launch shape starts at 512-thread CTAs with 1 block per lane per window
- * (see aes_batch_autotune).  AES_ENOMEM if its buffers cannot be allocated. */
+ * (1..2^24).  Its launch shape starts at 768-thread CTAs with 1 block per lane per window,
+ * which runs launches whose messages all use AES-128 keys and takes 512-thread CTAs for any
+ * other (see aes_batch_autotune).  AES_ENOMEM if its buffers cannot be allocated. */
 aes_status aes_batch_create(aes_keypool* pool, size_t max_msgs, aes_batch** out);
 
 /* Runs every message of `msgs` (host array of nmsgs <= max_msgs) reading d_in and writing
@@ -238,9 +239,10 @@ aes_status aes_batch_run(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const 
                          size_t buf_bytes, void* cuda_stream);
 
 /* Tunes the batch's launch shape on this workload: the CTA size and the blocks each lane
- * enciphers per window; compiled pairs are (512, 1), (512, 2), (512, 4), (384, 4), (256, 4),
- * one CTA per SM.  It
- * times every compiled candidate on `msgs` (it overwrites d_out), keeps the fastest and, if
+ * enciphers per window; compiled pairs are (512, 1), (512, 2), (512, 4), (384, 4), (256, 4)
+ * and, for work that is AES-128 throughout, (768, 1), one CTA per SM.  A direction whose
+ * messages all use AES-128 keys runs a kernel specialised to 10 rounds.  It
+ * times every candidate compiled for `msgs` (it overwrites d_out), keeps the fastest and, if
  * cache_path is not NULL, records it in that JSON file keyed by device name and workload
  * signature (an existing entry is reused without timing).  Writes the chosen shape to
  * *threads and *blocks_per_lane when they are not NULL. */

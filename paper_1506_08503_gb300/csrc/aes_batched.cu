@@ -34,7 +34,10 @@ struct Shape {
   int threads, bpl;
 };
 // (CTA threads, blocks each lane enciphers per window)
-constexpr Shape kShapes[] = {{512, 1}, {512, 2}, {512, 4}, {384, 4}, {256, 4}};
+// (768, 1) is compiled for AES-128 work only; a launch with other round counts at that shape
+// takes (512, 1).
+constexpr Shape kShapes[] = {{512, 1}, {512, 2}, {512, 4}, {384, 4}, {256, 4}, {768, 1}};
+constexpr int kMaxShapeThreads = 768;
 
 struct Slot {
   uint8_t* host = nullptr;  // pinned staging
@@ -44,14 +47,13 @@ struct Slot {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t kernel = nullptr;
-  int g_threads = 0, g_bpl = 0;
 };
 
 struct Layout {
   size_t enc_msgs, dec_msgs, enc_start, dec_start, enc_gb, dec_gb, enc_warp, dec_warp, end;
 };
 
-// wmax: most warps a launch can have (SMs x 512 threads / 32)
+// wmax: most warps a launch can have (SMs x the largest shape's threads / 32)
 Layout layout(size_t nenc, size_t ndec, size_t wmax) {
   Layout l;
   l.enc_msgs = 0;
@@ -110,7 +112,10 @@ struct aes_batch {
   size_t max_msgs = 0;
   size_t bytes = 0;
   size_t wmax = 0;
-  int threads = 512, bpl = 1;  // default shape (the autotuner may change it); measured on the served mix: 1 ~ 2 > 4
+  // default shape (the autotuner may change it): 768 threads, 1 block per lane where a launch's
+  // work is all AES-128 (0.84-0.85 of the plain kernel on the 4096-message workload, against
+  // 0.80-0.82 for 512 x 1), else 512 x 1 (on the served mix: 1 ~ 2 > 4 blocks per lane)
+  int threads = 768, bpl = 1;
   Slot slot[2];
   int next = 0;
   cudaStream_t copy_stream = nullptr;
@@ -158,15 +163,13 @@ cudaKernelNodeParams kernel_params(TTDualFn fn, unsigned grid, int threads, size
   return p;
 }
 
-aes_status build_graph(aes_batch* b, Slot& s, const cudaKernelNodeParams& p) {
+aes_status build_graph(Slot& s, const cudaKernelNodeParams& p) {
   if (s.exec) { cudaGraphExecDestroy(s.exec); s.exec = nullptr; }
   if (s.graph) { cudaGraphDestroy(s.graph); s.graph = nullptr; }
   cudaError_t e;
   if ((e = cudaGraphCreate(&s.graph, 0)) != cudaSuccess) return cuda_error(e, "cudaGraphCreate");
   if ((e = cudaGraphAddKernelNode(&s.kernel, s.graph, nullptr, 0, &p)) != cudaSuccess) return cuda_error(e, "cudaGraphAddKernelNode");
   if ((e = cudaGraphInstantiate(&s.exec, s.graph, 0)) != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
-  s.g_threads = b->threads;
-  s.g_bpl = b->bpl;
   return AES_OK;
 }
 
@@ -202,23 +205,34 @@ aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
 
   const DeviceInfo* di = current_device_info();
   if (!di) return AES_ECUDA;
-  TTDualFn fn = ttable_batched_dual(b->threads, b->bpl);
-  if (!fn) return set_error(AES_EINVAL, "shape (%d threads, %d blocks per lane) is not compiled", b->threads, b->bpl);
+  const int8_t* rounds = b->pool->nr;
+  const uint64_t we = work_of(em, nenc, rounds), wd = work_of(dm, ndec, rounds);
+  // AES-128 throughout a direction (work = 10 x blocks, as no key has fewer rounds) takes the
+  // specialised kernel; an empty direction takes the other's count
+  int nre = te && we == 10 * te ? 10 : 0, nrd = td && wd == 10 * td ? 10 : 0;
+  if (!te) nre = nrd;
+  if (!td) nrd = nre;
+  int threads = b->threads, bpl = b->bpl;
+  TTDualFn fn = ttable_batched_dual(threads, bpl, nre, nrd);
+  if (!fn && threads == 768) {
+    threads = 512;
+    bpl = 1;
+    fn = ttable_batched_dual(threads, bpl, nre, nrd);
+  }
+  if (!fn) return set_error(AES_EINVAL, "shape (%d threads, %d blocks per lane) is not compiled", threads, bpl);
   const size_t smem = ttable_smem_bytes(AES_DECRYPT);
   aes_status ast = ensure_smem_attr(fn, smem);
   if (ast != AES_OK) return ast;
   // one CTA per SM (fewer when there is less than one block per thread), split between the
   // directions in proportion to their work in round-blocks
-  const int8_t* rounds = b->pool->nr;
-  const uint64_t we = work_of(em, nenc, rounds), wd = work_of(dm, ndec, rounds);
-  const uint64_t per_cta = uint64_t(b->threads);
+  const uint64_t per_cta = uint64_t(threads);
   uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>(di->sms, (te + td + per_cta - 1) / per_cta));
   if (te && td) G = std::max<uint64_t>(G, 2);
   uint64_t ge = 0;
   if (!td) ge = G;
   else if (te) ge = std::min<uint64_t>(G - 1, std::max<uint64_t>(1, (G * we + (we + wd) / 2) / (we + wd)));
   const uint64_t gd = G - ge;
-  const uint64_t wpc = uint64_t(b->threads / 32), nwe = ge * wpc, nwd = gd * wpc;
+  const uint64_t wpc = uint64_t(threads / 32), nwe = ge * wpc, nwd = gd * wpc;
   if (nwe > b->wmax || nwd > b->wmax) return set_error(AES_ECUDA, "device has more SMs than the batch was sized for");
   weighted_slices(em, es, nenc, rounds, we, te ? nwe : 0, reinterpret_cast<uint64_t*>(h + L.enc_gb),
                   reinterpret_cast<uint32_t*>(h + L.enc_warp));
@@ -232,9 +246,9 @@ aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
                         reinterpret_cast<const uint32_t*>(s.dev + L.dec_warp), td, uint32_t(ndec), 0u,
                         reinterpret_cast<const uint64_t*>(s.dev + L.dec_gb)},
                b->pool->entries, uint32_t(ge), {}};
-  const cudaKernelNodeParams p = kernel_params(fn, unsigned(G), b->threads, smem, a);
-  if (!s.exec || s.g_threads != b->threads || s.g_bpl != b->bpl) {
-    aes_status st = build_graph(b, s, p);
+  const cudaKernelNodeParams p = kernel_params(fn, unsigned(G), threads, smem, a);
+  if (!s.exec) {  // a later launch with another kernel or shape updates the node in place
+    aes_status st = build_graph(s, p);
     if (st != AES_OK) return st;
   } else if ((e = cudaGraphExecKernelNodeSetParams(s.exec, s.kernel, &p)) != cudaSuccess) {
     return cuda_error(e, "cudaGraphExecKernelNodeSetParams");
@@ -291,6 +305,27 @@ aes_status run_locked(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const voi
     }
   };
   return batch_launch_descs(b, nenc, ndec, fill, reinterpret_cast<uint64_t>(d_in), reinterpret_cast<uint64_t>(d_out), stream);
+}
+
+// The round count every message of each direction has, as batch_launch_descs derives it from
+// the descriptors (10 for AES-128 throughout, else 0; an empty direction takes the other's).
+void round_classes(const aes_keypool* pool, const aes_msg* msgs, size_t n, int* nre, int* nrd) {
+  bool e_any = false, d_any = false, e10 = true, d10 = true;
+  for (size_t i = 0; i < n; ++i) {
+    if (msgs[i].length == 0) continue;
+    const bool ten = size_t(msgs[i].key_idx) < pool->capacity && pool->nr[msgs[i].key_idx] == 10;
+    if (msgs[i].dir == AES_ENCRYPT) {
+      e_any = true;
+      e10 &= ten;
+    } else {
+      d_any = true;
+      d10 &= ten;
+    }
+  }
+  *nre = e_any && e10 ? 10 : 0;
+  *nrd = d_any && d10 ? 10 : 0;
+  if (!e_any) *nre = *nrd;
+  if (!d_any) *nrd = *nre;
 }
 
 bool shape_compiled(int threads, int bpl) {
@@ -392,7 +427,7 @@ aes_status aes_batch_create(aes_keypool* pool, size_t max_msgs, aes_batch** out)
   if (b->device != pool->device) { delete b; return set_error(AES_EINVAL, "pool and batch on different devices"); }
   const DeviceInfo* di = current_device_info();
   if (!di) { delete b; return AES_ECUDA; }
-  b->wmax = size_t(di->sms) * (512 / 32);
+  b->wmax = size_t(di->sms) * (kMaxShapeThreads / 32);
   b->bytes = layout(max_msgs, max_msgs, b->wmax).end;  // enough for any split of max_msgs
   if ((e = cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) {
     delete b;
@@ -454,7 +489,10 @@ aes_status aes_batch_autotune(aes_batch* b, const aes_msg* msgs, size_t nmsgs, c
     double best = 1e30;
     Shape best_shape = kShapes[0];
     aes_status result = AES_OK;
+    int nre = 0, nrd = 0;
+    round_classes(b->pool, msgs, nmsgs, &nre, &nrd);
     for (const Shape& sh : kShapes) {
+      if (!ttable_batched_dual(sh.threads, sh.bpl, nre, nrd)) continue;  // (768, 1) on other than AES-128
       b->threads = sh.threads;
       b->bpl = sh.bpl;
       if ((result = run_locked(b, msgs, nmsgs, d_in, d_out, buf_bytes, st)) != AES_OK) break;  // warm-up, builds the graph

@@ -69,6 +69,33 @@ __device__ __forceinline__ void load_key(const PoolEntry* pool, uint32_t key, ui
   kl[0] = q.x; kl[1] = q.y; kl[2] = q.z; kl[3] = q.w;
 }
 
+// Round keys in registers: NRF + 1 rows when every message of the direction has NRF rounds;
+// for NRF = 0 (round counts mixed) the generic rows, the last key kl and the count nr read
+// with the key.
+template <int NRF>
+struct KeyRegs {
+  static constexpr int kRows = NRF ? NRF + 1 : kMaxRounds + 1;
+  uint32_t kw[kRows][4];
+  uint32_t kl[4];
+  int nr;
+};
+
+template <int DIR, int NRF>
+__device__ __forceinline__ void load_keys(const PoolEntry* pool, uint32_t key, KeyRegs<NRF>& k) {
+  if constexpr (NRF == 0) {
+    load_key<DIR>(pool, key, k.kw, k.kl, k.nr);
+  } else {
+    const PoolEntry* e = pool + key;
+    const uint4* kp = reinterpret_cast<const uint4*>(DIR == AES_ENCRYPT ? &e->enc[0][0] : &e->dec[0][0]);
+#pragma unroll
+    for (int r = 0; r <= NRF; ++r) {
+      const uint4 q = __ldg(kp + r);
+      k.kw[r][0] = q.x; k.kw[r][1] = q.y; k.kw[r][2] = q.z; k.kw[r][3] = q.w;
+    }
+    k.nr = NRF;
+  }
+}
+
 // Rounds 1..nr-1 of one block with the round keys in registers (nr = 10, 12 or 14; the
 // branches are warp-uniform on the fast path).
 template <int DIR>
@@ -88,6 +115,18 @@ __device__ __forceinline__ uint4 crypt_rt(uint4 v, const uint32_t (&kw)[kMaxRoun
   return tt_final<DIR>(s0, s1, s2, s3, kl[0], kl[1], kl[2], kl[3], sm, lc);
 }
 
+template <int DIR, int NRF>
+__device__ __forceinline__ uint4 crypt_keys(uint4 v, const KeyRegs<NRF>& k, const char* sm, uint32_t lc) {
+  if constexpr (NRF == 0) {
+    return crypt_rt<DIR>(v, k.kw, k.kl, k.nr, sm, lc);
+  } else {
+    uint32_t s0 = v.x ^ k.kw[0][0], s1 = v.y ^ k.kw[0][1], s2 = v.z ^ k.kw[0][2], s3 = v.w ^ k.kw[0][3];
+#pragma unroll
+    for (int r = 1; r < NRF; ++r) tt_round<DIR>(s0, s1, s2, s3, k.kw[r][0], k.kw[r][1], k.kw[r][2], k.kw[r][3], sm, lc);
+    return tt_final<DIR>(s0, s1, s2, s3, k.kw[NRF][0], k.kw[NRF][1], k.kw[NRF][2], k.kw[NRF][3], sm, lc);
+  }
+}
+
 // Warps step through their slice in windows of up to 32 * U blocks (lane l takes blocks
 // base + l + 32u) that never cross a message boundary: a window ends where its message ends.
 // The key, the round count and the source/destination bases are therefore the same for the
@@ -101,7 +140,9 @@ __device__ __forceinline__ uint4 crypt_rt(uint4 v, const uint32_t (&kw)[kMaxRoun
 // ahead; the first window issued before the table fill; a separate loop for whole windows,
 // whose second copy of the unrolled rounds costs more in instruction fetch than it saves.)
 // The work of CTA `cta` of the `ncta` CTAs given to one direction.
-template <int DIR, int THREADS, int U>
+// NRF != 0: every message of the direction has NRF rounds (the host checks), so the round
+// loop is fixed and the keys take NRF + 1 rows of registers.
+template <int DIR, int THREADS, int U, int NRF = 0>
 __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base, const BatchDir& bd,
                                              const PoolEntry* pool, uint32_t cta, uint32_t ncta, uint32_t* smem) {
   if (bd.total == 0) return;  // CTA-uniform, before any barrier
@@ -122,19 +163,17 @@ __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base
   }
   if (gb >= hi) return;  // warp-uniform; no barrier follows
 
-  uint32_t kw[kMaxRounds + 1][4];
-  uint32_t kl[4];
-  int nr = 0;
+  KeyRegs<NRF> k;
   Cursor c;  // warp-uniform: the message holding block gb
   open_msg(c, bd, bd.warp_msg ? __ldg(bd.warp_msg + w) : find_msg(bd.start, bd.nmsgs, gb));
-  load_key<DIR>(pool, c.key, kw, kl, nr);
+  load_keys<DIR, NRF>(pool, c.key, k);
   constexpr uint32_t kWin = 32u * U;
 
   while (gb < hi) {
     if (gb >= c.end) {
       const uint32_t old = c.key;
       seek(c, bd, gb);
-      if (c.key != old) load_key<DIR>(pool, c.key, kw, kl, nr);
+      if (c.key != old) load_keys<DIR, NRF>(pool, c.key, k);
     }
     uint64_t wend = gb + kWin;
     if (wend > hi) wend = hi;
@@ -176,7 +215,7 @@ __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base
       }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = crypt_rt<DIR>(v[u], kw, kl, nr, sm, lc);
+    for (int u = 0; u < U; ++u) v[u] = crypt_keys<DIR, NRF>(v[u], k, sm, lc);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t i = u * 32u + lane;
@@ -196,13 +235,14 @@ tt_batched_kernel(uint64_t in_base, uint64_t out_base, const BatchDir bd, const 
 // Both directions in one launch: CTAs [0, ge) encrypt, the others decrypt, so the two run
 // side by side instead of one after the other (one tail, one launch).  Each CTA fills only
 // its own direction's tables; the dynamic shared memory is sized for decryption.
-template <int THREADS, int U>
+// NRE / NRD: the round count of every encryption / decryption message, or 0 for mixed.
+template <int THREADS, int U, int NRE = 0, int NRD = 0>
 __global__ void __launch_bounds__(THREADS, 1)
 tt_batched_dual(uint64_t in_base, uint64_t out_base, const BatchDir be, const BatchDir bdd, const PoolEntry* pool,
                 uint32_t ge) {
   extern __shared__ __align__(16) uint32_t smem[];
-  if (blockIdx.x < ge) batched_body<AES_ENCRYPT, THREADS, U>(in_base, out_base, be, pool, blockIdx.x, ge, smem);
-  else batched_body<AES_DECRYPT, THREADS, U>(in_base, out_base, bdd, pool, blockIdx.x - ge, gridDim.x - ge, smem);
+  if (blockIdx.x < ge) batched_body<AES_ENCRYPT, THREADS, U, NRE>(in_base, out_base, be, pool, blockIdx.x, ge, smem);
+  else batched_body<AES_DECRYPT, THREADS, U, NRD>(in_base, out_base, bdd, pool, blockIdx.x - ge, gridDim.x - ge, smem);
 }
 
 }  // namespace tt

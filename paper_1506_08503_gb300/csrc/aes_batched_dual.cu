@@ -5,9 +5,12 @@
 
 namespace aesgb {
 
-TTDualFn ttable_batched_dual(int threads, int blocks_per_lane) {
+TTDualFn ttable_batched_dual(int threads, int blocks_per_lane, int nre, int nrd) {
+  if (nre == 10 || nrd == 10)
+    if (TTDualFn f = ttable_batched_dual_r10(threads, blocks_per_lane, nre, nrd)) return f;
   if (threads == 512 && blocks_per_lane == 1) return tt::tt_batched_dual<512, 1>;
   if (threads == 512 && blocks_per_lane == 2) return tt::tt_batched_dual<512, 2>;
+  if (threads == 768) return nullptr;  // 24 warps fit the registers only with AES-128 keys
   return ttable_batched_dual_wide(threads, blocks_per_lane);
 }
 

@@ -126,9 +126,13 @@ struct BatchDir {
 using TTBatchedFn = void (*)(uint64_t, uint64_t, const BatchDir, const PoolEntry*);
 // Both directions in one launch: the first `ge` CTAs encrypt, the rest decrypt.
 using TTDualFn = void (*)(uint64_t, uint64_t, const BatchDir, const BatchDir, const PoolEntry*, uint32_t);
-// Compiled shapes (CTA threads, blocks per lane per window); nullptr if not compiled.
-TTDualFn ttable_batched_dual(int threads, int blocks_per_lane);
+// Compiled shapes (CTA threads, blocks per lane per window) for nre / nrd, the round count
+// of every encryption / decryption message (0 when mixed); the kernel specialised to those
+// counts where one is compiled, else the generic one; nullptr if the shape is not compiled
+// for them.
+TTDualFn ttable_batched_dual(int threads, int blocks_per_lane, int nre, int nrd);
 TTDualFn ttable_batched_dual_wide(int threads, int blocks_per_lane);  // the U = 4 shapes
+TTDualFn ttable_batched_dual_r10(int threads, int blocks_per_lane, int nre, int nrd);  // AES-128 only
 
 }  // namespace aesgb
 
