@@ -105,30 +105,31 @@ def test_every_shape_gives_identical_output(aes_lib_ready):
 
 @pytest.mark.parametrize("case", ["enc128-decmixed", "encmixed-dec128", "both128", "dec128-only", "mixed"])
 def test_round_specialised_kernels(aes_lib_ready, orc, case):
-    """A direction whose messages all use AES-128 keys runs a kernel specialised to 10 rounds
-    (and the 768-thread shape exists only for AES-128 throughout); every combination of
-    specialised and generic directions, at every shape that has specialisations, matches the
-    oracle, and the 768-thread shape on mixed work falls back to the generic kernel."""
+    """A direction whose messages all use AES-128 keys runs a body specialised to 10 rounds (and
+    the 768-thread shape exists only for AES-128 throughout; other work set to that shape runs
+    the generic 512-thread kernel).  Every combination of specialised and generic directions,
+    with AES-128, -192 and -256 keys, at every shape that has specialisations, matches the
+    oracle."""
     import torch
 
     rng = np.random.default_rng(40 + len(case))
     n = 120
-    keys128 = rng.integers(0, 256, (n // 2, 16), dtype=np.uint8)
-    keys256 = rng.integers(0, 256, (n // 2, 32), dtype=np.uint8)
+    third = n // 3
+    keys = [rng.integers(0, 256, (third, b // 8), dtype=np.uint8) for b in (128, 192, 256)]
     lengths = (rng.integers(1, 200, n) * 16).astype(np.int64)
     offsets = np.concatenate([[0], np.cumsum(lengths)[:-1]]).astype(np.int64)
     data = rng.integers(0, 256, int(lengths.sum()), dtype=np.uint8)
     dirs = rng.integers(0, 2, n).astype(np.uint32)
     if case == "dec128-only":
         dirs[:] = 1
-    small = rng.integers(0, n // 2, n)           # AES-128 slots
-    any_ = rng.integers(0, n, n)                 # either size
+    small = rng.integers(0, third, n)            # AES-128 slots
+    any_ = rng.integers(0, n, n)                 # any size
     enc128 = case in ("enc128-decmixed", "both128")
     dec128 = case in ("encmixed-dec128", "both128", "dec128-only")
     key_idx = np.where(dirs == 0, np.where(enc128, small, any_), np.where(dec128, small, any_)).astype(np.uint32)
     with aes.KeyPool(n) as pool:
-        pool.load_keys(0, keys128, 128)
-        pool.load_keys(n // 2, keys256, 256)
+        for j, bits in enumerate((128, 192, 256)):
+            pool.load_keys(j * third, keys[j], bits)
         msgs = np.zeros(n, dtype=aes.msg_dtype())
         msgs["key_idx"], msgs["dir"], msgs["offset"], msgs["length"] = key_idx, dirs, offsets, lengths
         x = dev(data)
@@ -141,7 +142,7 @@ def test_round_specialised_kernels(aes_lib_ready, orc, case):
                 for i in range(n):
                     o, L = int(offsets[i]), int(lengths[i])
                     k = int(key_idx[i])
-                    key = keys128[k] if k < n // 2 else keys256[k - n // 2]
+                    key = keys[k // third][k % third]
                     f = orc.encrypt_blocks if dirs[i] == 0 else orc.decrypt_blocks
                     assert (got[o:o + L] == f(key, data[o:o + L], threads=THREADS)).all(), (shape, i)
 
