@@ -200,20 +200,27 @@ def run_reference(args):
     return 0
 
 
-def read_profile_traffic() -> tuple[float | None, tuple[int, int] | None]:
-    """DRAM bytes per launch of the encryption kernel and the (threads, blocks per thread) shape
-    they were taken on, from the committed ncu summary (its lines `traffic_bytes_per_launch: <n>`
-    and `profiled_shape: <threads>,<blocks per thread>`)."""
+def read_profile() -> dict:
+    """From the committed ncu summary of the T-table kernel: the (threads, blocks per thread)
+    shape it was taken on (`profiled_shape:`), DRAM bytes per 2^26-block launch per direction
+    (`traffic_bytes_per_launch:` for encryption, `..._decrypt:`) and per-direction counters
+    (`ncu_encrypt:` / `ncu_decrypt:`, key=value pairs)."""
     f = ROOT / "profiles" / "tt_kernel_aes128_256MiB.md"
-    traffic, shape = None, None
-    if f.exists():
-        for line in f.read_text().splitlines():
-            if line.startswith("traffic_bytes_per_launch:"):
-                traffic = float(line.split(":", 1)[1].split()[0])
-            if line.startswith("profiled_shape:"):
-                t, u = line.split(":", 1)[1].split()[0].split(",")
-                shape = (int(t), int(u))
-    return traffic, shape
+    out = {"shape": None, "traffic": {}, "ncu": {}, "source": f"profiles/{f.name}"}
+    if not f.exists():
+        return out
+    for line in f.read_text().splitlines():
+        key, _, rest = line.partition(":")
+        if key == "profiled_shape":
+            t, u = rest.split()[0].split(",")
+            out["shape"] = (int(t), int(u))
+        elif key == "traffic_bytes_per_launch":
+            out["traffic"]["encrypt"] = float(rest.split()[0])
+        elif key == "traffic_bytes_per_launch_decrypt":
+            out["traffic"]["decrypt"] = float(rest.split()[0])
+        elif key in ("ncu_encrypt", "ncu_decrypt"):
+            out["ncu"][key[4:]] = {k: float(v) for k, v in (kv.split("=") for kv in rest.split())}
+    return out
 
 
 def measure_batched(aes, torch, dev, steps: int, plain_gbs: float, fixed_shape=None) -> dict:
@@ -676,13 +683,14 @@ def run_ours(args):
     # the committed ncu traffic figure holds only for the shape it was taken on
     shape = tuned[dom] if tuned else {"impl": args.kernel if args.kernel != "auto" else "ttable", "threads": 512,
                                       "blocks_per_thread": 2}
-    prof_traffic, prof_shape = read_profile_traffic()
-    same_shape = shape["impl"] == "ttable" and (shape["threads"], shape["blocks_per_thread"]) == prof_shape
-    traffic = prof_traffic if same_shape and n == NBLOCKS else None
+    prof = read_profile()
+    same_shape = shape["impl"] == "ttable" and (shape["threads"], shape["blocks_per_thread"]) == prof["shape"]
+    traffic = prof["traffic"].get(dom) if same_shape and n == NBLOCKS else None
+    counters = dict(prof["ncu"][dom], source=prof["source"]) if same_shape and dom in prof["ncu"] else None
     kname = (f"tt_kernel<10,{dom},{shape['threads']},{shape['blocks_per_thread']}>" if shape["impl"] == "ttable"
              else f"bs_kernel<10,{dom}>")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": kname,
+                "traffic": traffic, "kernel": kname, "ncu": counters,
                 "peak_source": f"derived: {sms} SMs x {SM_MAX_MHZ_NOMINAL:.0f} MHz x {blocks_per_sm_clock():.4f} blocks/SM-clock x 16 B",
                 "enc_gbs": n * 16 / (enc_avg / 1e3) / 1e9, "dec_gbs": n * 16 / (dec_avg / 1e3) / 1e9,
                 "enc_gbs_median": n * 16 / (statistics.median(enc_ms) / 1e3) / 1e9,
