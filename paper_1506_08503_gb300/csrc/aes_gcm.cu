@@ -21,10 +21,15 @@
 // Multiplication by a fixed element M is linear, so it is one table lookup per 4-bit nibble
 // of the other operand: Y * M = XOR over the 32 nibbles j of T_j[nibble_j(Y)], with
 // T_j[v] = (v placed at nibble j) * M; a table is 32 x 16 entries of 16 bytes (8 KiB).  The
-// per-block multiplier Q sits in shared memory beside the AES T-tables, replicated 8 times
-// so that lane l reads copy (l mod 8), which occupies its own four banks: every 16-byte
-// lookup of a warp is exactly four conflict-free shared-memory wavefronts, whatever the
-// data.  The tree's multipliers H^(2^j) use unreplicated tables.
+// tree's multipliers H^(2^j) use such tables, unreplicated.  The per-block multiplier Q is
+// applied a byte at a time instead (Shoup's method): with B[b] = (b placed at byte 0) * Q,
+// Y * Q = sum_k x^(8k) B[y_k], evaluated by Horner's rule from byte 15 down; multiplying by
+// x^8 moves every byte up one place, and the byte pushed out of place 15 comes back as
+// R[o] = o * x^128 reduced (a two-byte value, the same for every key).  That is 16 lookups of
+// 16 bytes and 16 of 4 bytes per block, against 32 of 16 bytes with nibbles: 2.5 shared-memory
+// wavefronts per block instead of 4, for a few more shifts.  B is replicated 8 times (lane l
+// reads copy l mod 8, in its own four banks) and R 32 times (one copy per bank), so every
+// lookup is conflict free whatever the data; the two take the 64 KiB beside the AES tables.
 //
 // One launch on the caller's stream.  Every CTA derives what it needs itself (H and
 // Cipher(J0), H^(2^j) by repeated squaring, Q, the tables, from multiples M * x^i held in
@@ -48,7 +53,7 @@ constexpr size_t kCounter = kParts + kMaxCtas * 16;  // finished-CTA ticket (uin
 constexpr size_t kWorkBytes = kCounter + 16;
 constexpr int kThreads = 512;
 constexpr uint32_t kAesSmem = 2 * kRegion;            // encryption T-tables (128 KiB)
-constexpr uint32_t kMainSmem = kAesSmem + 65536;      // + replicated Q table
+constexpr uint32_t kMainSmem = kAesSmem + 65536;      // + the tables B and R of the Horner multiplier Q
 
 // Element as four big-endian words, w0 the most significant (bytes 0..3): the view in which
 // multiplying by x is a right shift.
@@ -142,18 +147,42 @@ __device__ __forceinline__ uint4 mul_tab(uint4 y, const uint4* tab) {
   return acc;
 }
 
-// y * Q with the replicated table: entry (j, v) of copy c at j*2048 + v*128 + c*16, and qb
-// already points at copy (lane mod 8).  The byte offset of v is one shift and one AND.
-__device__ __forceinline__ uint4 mul_q(uint4 y, const char* qb) {
-  uint4 acc = make_uint4(0, 0, 0, 0);
+// R[o]: the byte o pushed out of place 15 by a multiplication by x^8, reduced.  Bit 7 - m of o
+// is the coefficient of x^(120 + m), which becomes x^(128 + m) = x^m (1 + x + x^2 + x^7); the
+// result, of degree at most 14, is returned in the little-endian word view (bytes 0 and 1).
+__device__ __forceinline__ uint32_t fold8(uint32_t o) {
+  uint32_t r = 0;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const uint32_t w = j < 8 ? y.x : j < 16 ? y.y : j < 24 ? y.z : y.w;
-    const int s = 8 * ((j >> 1) & 3) + ((j & 1) ? 0 : 4);
-    const uint32_t off = s >= 7 ? (w >> (s - 7)) & 0x780u : (w << (7 - s)) & 0x780u;
-    acc = xor4(acc, *reinterpret_cast<const uint4*>(qb + j * 2048 + off));
+  for (int m = 0; m < 8; ++m)
+    if ((o >> (7 - m)) & 1u) {
+      const int e[4] = {m, m + 1, m + 2, m + 7};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) r ^= 1u << (8 * (e[q] >> 3) + 7 - (e[q] & 7));
+    }
+  return r;
+}
+
+// y * Q a byte at a time (see the header): Z = B[y_15], then Z = Z x^8 + B[y_k] for k = 14
+// down to 0, where Z x^8 is a left shift by 8 of the little-endian words plus R[byte 15].
+// mb points at this lane's copy of B (entry b at b * 128), rb at its copy of R (entry o at
+// o * 128); either offset is one shift and one AND of the byte.
+__device__ __forceinline__ uint4 mul_q8(uint4 y, const char* mb, const char* rb) {
+  const uint32_t w[4] = {y.x, y.y, y.z, y.w};
+  auto boff = [&](int k) -> uint32_t {
+    const int s = 8 * (k & 3);
+    return (s >= 7 ? (w[k >> 2] >> (s - 7)) : (w[k >> 2] << (7 - s))) & 0x7F80u;
+  };
+  uint4 z = *reinterpret_cast<const uint4*>(mb + boff(15));
+#pragma unroll
+  for (int k = 14; k >= 0; --k) {
+    const uint32_t r = *reinterpret_cast<const uint32_t*>(rb + ((z.w >> 17) & 0x7F80u));
+    const uint4 m = *reinterpret_cast<const uint4*>(mb + boff(k));
+    z.w = __funnelshift_l(z.z, z.w, 8) ^ m.w;
+    z.z = __funnelshift_l(z.y, z.z, 8) ^ m.z;
+    z.y = __funnelshift_l(z.x, z.y, 8) ^ m.y;
+    z.x = (z.x << 8) ^ r ^ m.x;
   }
-  return acc;
+  return z;
 }
 
 __device__ __forceinline__ uint4 shfl_down4(uint4 v, int d) {
@@ -221,7 +250,8 @@ __device__ void build_tables(const Be* ms, int count, Be* mx, uint4* tabs) {
 
 // ---- the whole GCM in one launch ------------------------------------------------------------
 // Every CTA: the AES T-tables; H = Cipher(0), Cipher(J0); the powers H^(2^j) by squaring;
-// Q = H^T; Q's table (8 copies, beside the T-tables); then the data pass (counter-mode AES
+// Q = H^T; Q's byte table B and the reduction table R (beside the T-tables); then the data
+// pass (counter-mode AES
 // and one GHASH Horner step per position); then the tree over its 512 threads.  The CTA that
 // finishes last (an atomic ticket; nobody waits) combines the CTAs' partial sums and writes
 // the tag.
@@ -266,18 +296,36 @@ gcm_kernel(const GcmArgs g, const KeyWords kw, char* work, uint8_t* tag, uint64_
     if (tid == 0) s_ms[0] = q;
   }
   __syncthreads();
-  Be* qmx = qscratch + 18 * 128;  // Q's multiples, after the factors' (still inside the region)
-  for (uint32_t i = tid; i < 128; i += kThreads) qmx[i] = mulx(s_ms[0], int(i));
+  Be* qmx = qscratch + 18 * 128;  // Q * x^i, i < 8, after the factors' (still inside the region)
+  if (tid < 8) qmx[tid] = mulx(s_ms[0], int(tid));
   __syncthreads();
-  const uint4 qe = entry_from_multiples(qmx, int(tid >> 4), int(tid & 15u));
-  __syncthreads();  // every entry is read before the table overwrites the scratch
-  {
-    uint4* qtab = reinterpret_cast<uint4*>(smc + kAesSmem);
+  // threads 0..255: entry tid of B (bit 7 - i of the byte is the coefficient of x^i);
+  // threads 256..511: entry tid - 256 of R
+  static_assert(kThreads == 512, "B and R take one entry per thread");
+  uint4 be = make_uint4(0, 0, 0, 0);
+  uint32_t re = 0;
+  if (tid < 256) {
+    Be acc{0, 0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < 8; ++c) qtab[tid * 8 + c] = qe;
+    for (int i = 0; i < 8; ++i)
+      if ((tid >> (7 - i)) & 1u) acc = bxor(acc, qmx[i]);
+    be = to_le(acc);
+  } else {
+    re = fold8(tid - 256u);
+  }
+  __syncthreads();  // every multiple is read before the tables overwrite the scratch
+  if (tid < 256) {
+    uint4* btab = reinterpret_cast<uint4*>(smc + kAesSmem);  // entry b, copy c at b * 128 + c * 16
+#pragma unroll
+    for (int c = 0; c < 8; ++c) btab[tid * 8 + c] = be;
+  } else {
+    uint4* rtab = reinterpret_cast<uint4*>(smc + kAesSmem + 32768);  // entry o, copy l at o * 128 + l * 4
+#pragma unroll
+    for (int c = 0; c < 8; ++c) rtab[(tid - 256u) * 8 + c] = make_uint4(re, re, re, re);
   }
   __syncthreads();
-  const char* qb = sm + kAesSmem + (lane & 7u) * 16u;
+  const char* mb = sm + kAesSmem + (lane & 7u) * 16u;
+  const char* rb = sm + kAesSmem + 32768 + lc;
   const uint64_t TT = T;
   const uint64_t t = uint64_t(blockIdx.x) * kThreads + tid;
   const uint64_t cblocks = (g.len + 15) / 16;
@@ -328,7 +376,7 @@ gcm_kernel(const GcmArgs g, const KeyWords kw, char* work, uint8_t* tag, uint64_
             h = make_uint4(o.x & byte_mask(nb, 0), o.y & byte_mask(nb, 1), o.z & byte_mask(nb, 2), o.w & byte_mask(nb, 3));
         }
       }
-      if (k + u < g.K) y = xor4(mul_q(y, qb), h);
+      if (k + u < g.K) y = xor4(mul_q8(y, mb, rb), h);
     }
   }
 
