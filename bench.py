@@ -21,6 +21,7 @@ checked against), on a bounded sample per step.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -471,13 +472,21 @@ def measure_served(aes, torch, dev, nreq: int, plain_gbs: float) -> dict:
             tickets = []
             t0 = _t.perf_counter()
             if rate:
-                for i in range(len(w.lengths)):
-                    target = t0 + w.arrival_s[i]
-                    while _t.perf_counter() < target:
-                        pass
-                    o = int(offs[i])
-                    tickets.append(srv.submit(int(w.key_idx[i]), int(w.dirs[i]), sp + o, dp + o, int(w.lengths[i]),
-                                              True, True))
+                # the client's own pauses would show as bursts in the offered load: no Python
+                # garbage collection while it submits (the server's threads are native)
+                arrivals, kidx, dirs, lens = (w.arrival_s.tolist(), w.key_idx.tolist(), w.dirs.tolist(),
+                                              w.lengths.tolist())
+                offl = offs.tolist()
+                gc.disable()
+                try:
+                    for i in range(len(lens)):
+                        target = t0 + arrivals[i]
+                        while _t.perf_counter() < target:
+                            pass
+                        o = offl[i]
+                        tickets.append(srv.submit(kidx[i], dirs[i], sp + o, dp + o, lens[i], True, True))
+                finally:
+                    gc.enable()
             else:  # closed loop: the whole workload queued in bulk, the server batches what it finds;
                 # three repetitions, the median one reported (the loop leans on host threads)
                 reqs = np.zeros(len(w.lengths), dtype=aes.request_dtype())
