@@ -79,6 +79,7 @@ def _declare(l: ctypes.CDLL) -> ctypes.CDLL:
         "oracle_gf128_mul": (None, [_U8P, _U8P, _U8P]),
         "oracle_ghash": (None, [_U8P, _U8P, sz, _U8P]),
         "oracle_gcm_crypt": (None, [_U8P, i, _U8P, _U8P, sz, _U8P, _U8P, sz, i, _U8P]),
+        "oracle_gcm_crypt_iv": (None, [_U8P, i, _U8P, sz, _U8P, sz, _U8P, _U8P, sz, i, _U8P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(l, name)
@@ -206,16 +207,16 @@ class Oracle:
     def gcm_crypt(self, key, iv, data, aad=b"", decrypt: bool = False) -> tuple[np.ndarray, np.ndarray]:
         """(output bytes, tag); the data and AAD may have any length."""
         rk, nr = self.key_expand(key)
-        ivv = _u8(iv)
-        if ivv.size != 12:
-            raise ValueError("the GCM oracle takes 96-bit IVs")
+        ivv = _u8(iv).reshape(-1)
+        if ivv.size == 0:
+            raise ValueError("a GCM IV has at least one byte")
         src = _u8(data).reshape(-1)
         a = _u8(aad).reshape(-1)
         out = np.empty_like(src)
         tag = np.empty(16, dtype=np.uint8)
-        self.lib.oracle_gcm_crypt(_p(rk), nr, _p(ivv), _p(a) if a.size else None, a.size,
-                                  _p(src) if src.size else None, _p(out) if src.size else None, src.size,
-                                  int(decrypt), _p(tag))
+        self.lib.oracle_gcm_crypt_iv(_p(rk), nr, _p(ivv), ivv.size, _p(a) if a.size else None, a.size,
+                                     _p(src) if src.size else None, _p(out) if src.size else None, src.size,
+                                     int(decrypt), _p(tag))
         return out, tag
 
 

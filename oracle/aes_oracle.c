@@ -35,8 +35,9 @@
  *   - the Galois/Counter Mode, the counter-based authenticated mode that Section V names as
  *     future work.  The paper does not define it; this follows NIST SP 800-38D: the
  *     GF(2^128) product bit by bit (its Algorithm 1), GHASH as Horner's rule (Algorithm 2),
- *     and GCM with a 96-bit IV (Algorithms 4 and 5: J0 = IV || 0^31 || 1, data counters
- *     from inc32(J0), tag = Cipher(J0) + GHASH(A, C, lengths)); pinned against OpenSSL's GCM
+ *     and GCM (Algorithms 4 and 5: J0 = IV || 0^31 || 1 for a 96-bit IV, else GHASH of
+ *     the zero-padded IV and its bit length; data counters from inc32(J0); tag =
+ *     Cipher(J0) + GHASH(A, C, lengths)); pinned against OpenSSL's GCM
  *
  * Parity is pinned by the test suite (GF brute force, field and S-box invariants, the
  * paper's worked examples, and bit-exact agreement with OpenSSL's AES).
@@ -419,25 +420,36 @@ static void ghash_step(uint8_t acc[16], const uint8_t h[16], const uint8_t* blk,
   oracle_gf128_mul(acc, h, acc);
 }
 
-/* GCM with a 96-bit IV (SP 800-38D Algorithms 4 and 5).  H = Cipher(0^128); J0 = IV || 0^31
- * || 1; data block j is XORed with Cipher(J0 with its last 32 bits set to 2 + j mod 2^32);
- * the hash runs over the AAD and the ciphertext, each zero-padded to whole blocks, then the
- * block [64-bit bit length of AAD || 64-bit bit length of the ciphertext]; the tag is
- * Cipher(J0) + that hash. */
-void oracle_gcm_crypt(const uint8_t* rk, int nr, const uint8_t iv[12], const uint8_t* aad, size_t aad_len,
-                      const uint8_t* in, uint8_t* out, size_t len, int decrypt, uint8_t tag[16]) {
+/* GCM (SP 800-38D Algorithms 4 and 5).  H = Cipher(0^128).  J0 = IV || 0^31 || 1 for a
+ * 96-bit IV; for any other length, J0 = GHASH_H(IV zero-padded to whole blocks || a block
+ * holding 0^64 and the 64-bit bit length of the IV).  Data block j is XORed with
+ * Cipher(J0 with its last 32 bits increased by 1 + j, mod 2^32); the hash runs over the AAD
+ * and the ciphertext, each zero-padded to whole blocks, then the block [64-bit bit length of
+ * AAD || 64-bit bit length of the ciphertext]; the tag is Cipher(J0) + that hash. */
+void oracle_gcm_crypt_iv(const uint8_t* rk, int nr, const uint8_t* iv, size_t iv_len, const uint8_t* aad,
+                         size_t aad_len, const uint8_t* in, uint8_t* out, size_t len, int decrypt, uint8_t tag[16]) {
   uint8_t h[16], j0[16], ctr[16], ks[16], acc[16], blk[16];
   memset(h, 0, 16);
   oracle_encrypt_block(rk, nr, NULL, h, h);
-  memcpy(j0, iv, 12);
-  j0[12] = 0; j0[13] = 0; j0[14] = 0; j0[15] = 1;
+  if (iv_len == 12) {
+    memcpy(j0, iv, 12);
+    j0[12] = 0; j0[13] = 0; j0[14] = 0; j0[15] = 1;
+  } else {
+    memset(j0, 0, 16);
+    for (size_t off = 0; off < iv_len; off += 16) ghash_step(j0, h, iv + off, iv_len - off < 16 ? iv_len - off : 16);
+    const uint64_t ivbits = (uint64_t)iv_len * 8u;
+    memset(blk, 0, 16);
+    for (int k = 0; k < 8; ++k) blk[8 + k] = (uint8_t)(ivbits >> (56 - 8 * k));
+    ghash_step(j0, h, blk, 16);
+  }
+  const uint32_t c0 = ((uint32_t)j0[12] << 24) | ((uint32_t)j0[13] << 16) | ((uint32_t)j0[14] << 8) | j0[15];
   memset(acc, 0, 16);
   for (size_t off = 0; off < aad_len; off += 16)
     ghash_step(acc, h, aad + off, aad_len - off < 16 ? aad_len - off : 16);
   memcpy(ctr, j0, 12);
   for (size_t j = 0; 16 * j < len; ++j) {
     const size_t off = 16 * j, nb = len - off < 16 ? len - off : 16;
-    const uint32_t c = (uint32_t)(2u + (uint32_t)j); /* inc32 wraps mod 2^32 */
+    const uint32_t c = (uint32_t)(c0 + 1u + (uint32_t)j); /* inc32 wraps mod 2^32 */
     ctr[12] = (uint8_t)(c >> 24); ctr[13] = (uint8_t)(c >> 16); ctr[14] = (uint8_t)(c >> 8); ctr[15] = (uint8_t)c;
     oracle_encrypt_block(rk, nr, NULL, ctr, ks);
     memcpy(blk, in + off, nb); /* the ciphertext of a decryption, before in == out overwrites it */
@@ -452,4 +464,9 @@ void oracle_gcm_crypt(const uint8_t* rk, int nr, const uint8_t iv[12], const uin
   ghash_step(acc, h, blk, 16);
   oracle_encrypt_block(rk, nr, NULL, j0, ks);
   for (int k = 0; k < 16; ++k) tag[k] = (uint8_t)(ks[k] ^ acc[k]);
+}
+
+void oracle_gcm_crypt(const uint8_t* rk, int nr, const uint8_t iv[12], const uint8_t* aad, size_t aad_len,
+                      const uint8_t* in, uint8_t* out, size_t len, int decrypt, uint8_t tag[16]) {
+  oracle_gcm_crypt_iv(rk, nr, iv, 12, aad, aad_len, in, out, len, decrypt, tag);
 }

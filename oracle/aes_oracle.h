@@ -69,8 +69,12 @@ void oracle_ctr_crypt(const uint8_t* rk, int nr, const uint8_t ctr0[16], const u
 void oracle_gf128_mul(const uint8_t x[16], const uint8_t y[16], uint8_t z[16]);
 /* GHASH_H over nblocks whole blocks: Y_0 = 0, Y_i = (Y_{i-1} + X_i) * H */
 void oracle_ghash(const uint8_t h[16], const uint8_t* x, size_t nblocks, uint8_t y[16]);
-/* AES-GCM with a 96-bit IV; decrypt != 0 hashes `in` (the ciphertext) instead of `out`.
- * Writes len bytes to out and the 16-byte tag.  in == out is allowed. */
+/* AES-GCM with an IV of iv_len >= 1 bytes (96 bits: J0 = IV || 0^31 || 1; otherwise J0 by
+ * GHASH of the IV and its length); decrypt != 0 hashes `in` (the ciphertext) instead of
+ * `out`.  Writes len bytes to out and the 16-byte tag.  in == out is allowed. */
+void oracle_gcm_crypt_iv(const uint8_t* rk, int nr, const uint8_t* iv, size_t iv_len, const uint8_t* aad,
+                         size_t aad_len, const uint8_t* in, uint8_t* out, size_t len, int decrypt, uint8_t tag[16]);
+/* the same with a 96-bit IV */
 void oracle_gcm_crypt(const uint8_t* rk, int nr, const uint8_t iv[12], const uint8_t* aad, size_t aad_len,
                       const uint8_t* in, uint8_t* out, size_t len, int decrypt, uint8_t tag[16]);
 

@@ -9,6 +9,9 @@ names as future work; defined by NIST SP 800-38D, not by the paper).
 - Whole GCM encryption and decryption, bit-exact against OpenSSL's AES-GCM (through the
   `cryptography` package) for 128/192/256-bit keys, empty and ragged data and AAD.
 - A flipped ciphertext block changes the tag by exactly delta * H^e.
+- IVs other than 96 bits (J0 by GHASH of the IV): against OpenSSL for 8 to 128 bytes, and for
+  lengths OpenSSL refuses (1, 7, 129 to 256 bytes) against GCM composed by definition from the
+  separately pinned GHASH, counter mode and block cipher.
 """
 import numpy as np
 import pytest
@@ -152,3 +155,54 @@ def test_gcm_tag_difference_is_delta_times_power(orc):
         ct2[16 * j:16 * j + 16] ^= delta
         _, t1 = orc.gcm_crypt(key, iv, ct2, aad, decrypt=True)
         assert ((t0 ^ t1) == orc.gf128_mul(delta, power(orc, h, c - j + 1))).all()
+
+
+@pytest.mark.parametrize("iv_len", [8, 13, 16, 20, 32, 60, 64, 128])
+def test_gcm_any_iv_length_matches_openssl(orc, iv_len):
+    # IVs other than 96 bits take J0 = GHASH_H(IV, zero-padded, || 0^64 || bit length of IV)
+    # (SP 800-38D); OpenSSL accepts 8 to 128 bytes
+    AESGCM = _aesgcm()
+    rng = np.random.default_rng(200 + iv_len)
+    for key_bytes in (16, 24, 32):
+        for length, alen in ((0, 0), (1, 0), (37, 5), (1000, 33)):
+            key, iv = rnd(rng, key_bytes), rnd(rng, iv_len)
+            pt, aad = rnd(rng, length), rnd(rng, alen)
+            ct, tag = orc.gcm_crypt(key, iv, pt, aad)
+            ref = AESGCM(key.tobytes()).encrypt(iv.tobytes(), pt.tobytes(), aad.tobytes() if alen else None)
+            assert ct.tobytes() + tag.tobytes() == ref, (key_bytes, length, alen)
+            back, tag2 = orc.gcm_crypt(key, iv, ct, aad, decrypt=True)
+            assert (back == pt).all() and (tag2 == tag).all()
+
+
+def _pad(b):
+    return np.concatenate([b, np.zeros(-b.size % 16, dtype=np.uint8)])
+
+
+def _lengths(a_bytes, c_bytes):
+    return np.frombuffer(int(8 * a_bytes).to_bytes(8, "big") + int(8 * c_bytes).to_bytes(8, "big"), dtype=np.uint8)
+
+
+@pytest.mark.parametrize("iv_len", [1, 7, 129, 200, 256])
+def test_gcm_iv_outside_openssl_range_by_composition(orc, iv_len):
+    # lengths OpenSSL refuses: GCM composed from the separately pinned GHASH, counter mode and
+    # block cipher, following the definitions (J0 by GHASH; counters inc32(J0) + 1 + j, here
+    # without a 32-bit wrap, which the test checks; tag = Cipher(J0) + GHASH(A, C, lengths))
+    rng = np.random.default_rng(300 + iv_len)
+    key, iv = rnd(rng, 16), rnd(rng, iv_len)
+    pt, aad = rnd(rng, 100), rnd(rng, 20)
+    h = orc.encrypt_blocks(key, np.zeros(16, dtype=np.uint8))
+    j0 = orc.ghash(h, np.concatenate([_pad(iv), _lengths(0, iv_len)]))
+    low = int.from_bytes(j0[12:].tobytes(), "big")
+    assert low + 1 + 7 < 2 ** 32  # no inc32 wrap over the 7 data blocks
+    ctr1 = j0.copy()
+    ctr1[12:] = np.frombuffer((low + 1).to_bytes(4, "big"), dtype=np.uint8)
+    stream = orc.ctr_crypt(key, ctr1, np.zeros(112, dtype=np.uint8))
+    ct_ref = pt ^ stream[:100]
+    tag_ref = orc.encrypt_blocks(key, j0) ^ orc.ghash(h, np.concatenate([_pad(aad), _pad(ct_ref), _lengths(20, 100)]))
+    ct, tag = orc.gcm_crypt(key, iv, pt, aad)
+    assert (ct == ct_ref).all() and (tag == tag_ref).all()
+    # and the 96-bit special case really is special: a 12-byte IV does not take the GHASH route
+    iv12 = rnd(rng, 12)
+    j0_12 = np.concatenate([iv12, np.array([0, 0, 0, 1], dtype=np.uint8)])
+    _, t12 = orc.gcm_crypt(key, iv12, b"", b"")
+    assert (t12 == orc.encrypt_blocks(key, j0_12) ^ orc.ghash(h, _lengths(0, 0))).all()
