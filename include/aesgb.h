@@ -133,12 +133,14 @@ aes_status aes_ctr_crypt(const aes_key_schedule* ks, const uint8_t* ctr0, const 
                          size_t nblocks, void* cuda_stream);
 
 /* AES-GCM, the counter-based authenticated mode that Section V of the paper names as future
- * work; the paper does not define it, so this follows NIST SP 800-38D with a 96-bit IV.
- * Data block j is XORed with Cipher(IV || 2 + j mod 2^32) (the last 32 bits count, big-endian,
- * from J0 = IV || 0^31 || 1), and the 16-byte tag is Cipher(J0) + GHASH_H over the AAD and
- * the ciphertext (each zero-padded to whole blocks) and the two bit lengths, H = Cipher(0).
+ * work; the paper does not define it, so this follows NIST SP 800-38D.  J0 = IV || 0^31 || 1
+ * for a 96-bit IV, else GHASH_H of the IV zero-padded to whole blocks and a block holding its
+ * 64-bit bit length (computed in the kernel).  Data block j is XORed with Cipher(J0 with its
+ * last 32 bits, big-endian, increased by 1 + j mod 2^32), and the 16-byte tag is Cipher(J0) +
+ * GHASH_H over the AAD and the ciphertext (each zero-padded to whole blocks) and the two bit
+ * lengths, H = Cipher(0).
  *   ks         any schedule from aes_key_expand (AES-128/192/256)
- *   iv, iv_len host IV; iv_len must be 12 (other IV lengths are not supported: AES_EINVAL)
+ *   iv, iv_len host IV of 1 to 256 bytes (12 is the recommended length); else AES_EINVAL
  *   d_aad      device, aad_len bytes (any length up to 64 GiB, 16-byte aligned pointer),
  *              authenticated, not encrypted; may be NULL when aad_len is 0
  *   d_in/d_out device, nbytes bytes (any length up to (2^32 - 2) * 16), 16-byte aligned;

@@ -233,9 +233,34 @@ struct GcmArgs {
   uint64_t aad_len;  // bytes
   uint64_t len;      // data bytes
   uint32_t K;        // positions per thread
-  uint32_t iv0, iv1, iv2;
+  uint4 j0;          // J0 of a 96-bit IV (IV || 0^31 || 1); ignored when IvHash::n > 0
   int decrypt;
 };
+
+// For an IV other than 96 bits: the blocks GHASH runs over to give J0 (the IV zero-padded to
+// whole blocks, then 0^64 and the IV's bit length), as little-endian words; n = 0 means that
+// GcmArgs::j0 holds J0 directly.
+constexpr int kMaxIvBytes = 256;
+struct IvHash {
+  uint4 b[kMaxIvBytes / 16 + 1];
+  uint32_t n;
+};
+
+// J0 = GHASH_H over ivh's blocks, by the 32 lanes of one warp (all must call it): hmx (128
+// entries of shared memory) receives the multiples H * x^i for warp_mul.
+__device__ uint4 j0_from_iv(const IvHash& ivh, Be h, Be* hmx) {
+  const int l = int(threadIdx.x & 31u);
+  for (int i = l; i < 128; i += 32) hmx[i] = mulx(h, i);
+  __syncwarp();
+  Be y{0, 0, 0, 0};
+  for (uint32_t b = 0; b < ivh.n; ++b) y = warp_mul(bxor(y, to_be(ivh.b[b])), hmx);
+  return to_le(y);
+}
+
+// Counter block of data block j: J0 with its last 32 bits (big-endian) increased by 1 + j.
+__device__ __forceinline__ uint4 counter_block(uint4 j0, uint64_t j) {
+  return make_uint4(j0.x, j0.y, j0.z, bswap32(bswap32(j0.w) + 1u + uint32_t(j)));
+}
 
 // Builds, into tabs[k * 512 ..], the nibble tables of the multipliers ms[k] (k < count), using
 // mx (count * 128 entries) as scratch for the multiples M * x^i.  All threads of the CTA
@@ -257,9 +282,11 @@ __device__ void build_tables(const Be* ms, int count, Be* mx, uint4* tabs) {
 // the tag.
 template <int NR, int U>
 __global__ void __launch_bounds__(kThreads, 1)
-gcm_kernel(const GcmArgs g, const KeyWords kw, char* work, uint8_t* tag, uint64_t abits, uint64_t cbits) {
+gcm_kernel(const GcmArgs g, const KeyWords kw, const IvHash ivh, char* work, uint8_t* tag, uint64_t abits,
+           uint64_t cbits) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint4 s_he[2];
+  __shared__ uint4 s_he[2];  // Cipher(0) = H and Cipher(J0)
+  __shared__ uint4 s_j0;
   __shared__ Be s_pow[18];
   __shared__ Be s_ms[9];
   __shared__ uint4 s_warp[kThreads / 32];
@@ -270,11 +297,23 @@ gcm_kernel(const GcmArgs g, const KeyWords kw, char* work, uint8_t* tag, uint64_
   const uint32_t lc = lane * 4u;
   fill_tables<AES_ENCRYPT>(smem);
   __syncthreads();
-  if (tid < 2) {
-    const uint4 v = tid ? make_uint4(g.iv0, g.iv1, g.iv2, bswap32(1u)) : make_uint4(0, 0, 0, 0);
-    s_he[tid] = crypt_block<NR, AES_ENCRYPT>(v, kw, sm, lc);
+  if (tid == 0) s_he[0] = crypt_block<NR, AES_ENCRYPT>(make_uint4(0, 0, 0, 0), kw, sm, lc);
+  if (tid == 32 && ivh.n == 0) {
+    s_j0 = g.j0;
+    s_he[1] = crypt_block<NR, AES_ENCRYPT>(g.j0, kw, sm, lc);
   }
   __syncthreads();
+  if (ivh.n) {  // uniform: J0 by GHASH of the IV, in the first warp (the Q region is free yet)
+    if (tid < 32) {
+      const uint4 j0 = j0_from_iv(ivh, to_be(s_he[0]), reinterpret_cast<Be*>(smc + kAesSmem));
+      if (tid == 0) {
+        s_j0 = j0;
+        s_he[1] = crypt_block<NR, AES_ENCRYPT>(j0, kw, sm, lc);
+      }
+    }
+    __syncthreads();
+  }
+  const uint4 j0 = s_j0;
   if (tid == 0) {
     Be p = to_be(s_he[0]);
     s_pow[0] = p;
@@ -356,7 +395,7 @@ gcm_kernel(const GcmArgs g, const KeyWords kw, char* work, uint8_t* tag, uint64_
                                         : ld_partial(reinterpret_cast<const uint8_t*>(g.in) + 16 * jb, uint32_t(g.len - 16 * jb));
         }
       }
-      ctr[u] = make_uint4(g.iv0, g.iv1, g.iv2, bswap32(uint32_t(2u + uint32_t(idx[u]))));
+      ctr[u] = counter_block(j0, idx[u]);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) ctr[u] = crypt_block<NR, AES_ENCRYPT>(ctr[u], kw, sm, lc);
@@ -434,24 +473,30 @@ gcm_kernel(const GcmArgs g, const KeyWords kw, char* work, uint8_t* tag, uint64_
 }
 
 // No hashed block at all (empty AAD and data): the tag is Cipher(J0) + (0 + L) * H with L = 0,
-// i.e. Cipher(J0).  One thread.
+// i.e. Cipher(J0).  One warp (J0 by GHASH for an IV other than 96 bits), one thread writes.
 template <int NR>
-__global__ void __launch_bounds__(kThreads, 1) gcm_empty_kernel(const KeyWords kw, uint32_t iv0, uint32_t iv1, uint32_t iv2,
+__global__ void __launch_bounds__(kThreads, 1) gcm_empty_kernel(const KeyWords kw, const uint4 j0_direct, const IvHash ivh,
                                                                uint8_t* tag) {
   extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ Be s_hmx[128];
   fill_tables<AES_ENCRYPT>(smem);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const uint4 e = crypt_block<NR, AES_ENCRYPT>(make_uint4(iv0, iv1, iv2, bswap32(1u)), kw,
-                                                 reinterpret_cast<const char*>(smem), 0u);
-    const uint32_t tw[4] = {e.x, e.y, e.z, e.w};
-    for (int b = 0; b < 16; ++b) tag[b] = uint8_t(tw[b >> 2] >> (8 * (b & 3)));
+  if (threadIdx.x < 32) {
+    const char* sm = reinterpret_cast<const char*>(smem);
+    const uint32_t lc = (threadIdx.x & 31u) * 4u;
+    uint4 j0 = j0_direct;
+    if (ivh.n) j0 = j0_from_iv(ivh, to_be(crypt_block<NR, AES_ENCRYPT>(make_uint4(0, 0, 0, 0), kw, sm, lc)), s_hmx);
+    if (threadIdx.x == 0) {
+      const uint4 e = crypt_block<NR, AES_ENCRYPT>(j0, kw, sm, lc);
+      const uint32_t tw[4] = {e.x, e.y, e.z, e.w};
+      for (int b = 0; b < 16; ++b) tag[b] = uint8_t(tw[b >> 2] >> (8 * (b & 3)));
+    }
   }
 }
 
 constexpr int kUnroll = 2;
-using GcmFn = void (*)(const GcmArgs, const KeyWords, char*, uint8_t*, uint64_t, uint64_t);
-using EmptyFn = void (*)(const KeyWords, uint32_t, uint32_t, uint32_t, uint8_t*);
+using GcmFn = void (*)(const GcmArgs, const KeyWords, const IvHash, char*, uint8_t*, uint64_t, uint64_t);
+using EmptyFn = void (*)(const KeyWords, const uint4, const IvHash, uint8_t*);
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
@@ -471,7 +516,8 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
   clear_error();
   if (!schedule_ok(ks)) return set_error(AES_EINVAL, "invalid key schedule (nr must be 10, 12 or 14)");
   if (dir != AES_ENCRYPT && dir != AES_DECRYPT) return set_error(AES_EINVAL, "dir must be AES_ENCRYPT or AES_DECRYPT");
-  if (!iv || iv_len != 12) return set_error(AES_EINVAL, "GCM takes a 12-byte (96-bit) IV");
+  if (!iv || iv_len == 0 || iv_len > size_t(kMaxIvBytes))
+    return set_error(AES_EINVAL, "GCM takes an IV of 1 to %d bytes", kMaxIvBytes);
   if (!d_tag) return set_error(AES_EINVAL, "null tag");
   if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & 15u) || work_bytes < kWorkBytes)
     return set_error(AES_EINVAL, "workspace must be 16-byte aligned and at least %zu bytes", kWorkBytes);
@@ -497,8 +543,28 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
   const uint64_t want = (n + kThreads - 1) / kThreads;  // at least one position per thread
   const uint32_t nb = n == 0 ? 0u : uint32_t(want < 1 ? 1 : want > uint64_t(max_ctas) ? uint64_t(max_ctas) : want);
   const uint32_t T = (nb ? nb : 1u) * kThreads;
-  uint32_t ivw[3];
-  std::memcpy(ivw, iv, 12);
+  // J0 directly for a 96-bit IV; otherwise the blocks its GHASH runs over (in the kernel)
+  uint4 j0{0u, 0u, 0u, 0u};
+  IvHash ivh{};
+  if (iv_len == 12) {
+    uint32_t ivw[3];
+    std::memcpy(ivw, iv, 12);
+    j0 = make_uint4(ivw[0], ivw[1], ivw[2], 0x01000000u);  // bytes 12..15 = 0, 0, 0, 1
+  } else {
+    const size_t nblk = (iv_len + 15) / 16;
+    uint8_t bytes[(kMaxIvBytes / 16 + 1) * 16] = {};
+    std::memcpy(bytes, iv, iv_len);
+    const uint64_t ivbits = uint64_t(iv_len) * 8u;
+    for (int k = 0; k < 8; ++k) bytes[nblk * 16 + 8 + k] = uint8_t(ivbits >> (56 - 8 * k));
+    for (size_t i = 0; i <= nblk; ++i) {
+      uint32_t w[4];
+      for (int q = 0; q < 4; ++q)
+        w[q] = uint32_t(bytes[16 * i + 4 * q]) | (uint32_t(bytes[16 * i + 4 * q + 1]) << 8) |
+               (uint32_t(bytes[16 * i + 4 * q + 2]) << 16) | (uint32_t(bytes[16 * i + 4 * q + 3]) << 24);
+      ivh.b[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    ivh.n = uint32_t(nblk + 1);
+  }
   const KeyWords kw = enc_key_words(*ks, nullptr);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   char* work = static_cast<char*>(d_work);
@@ -508,7 +574,7 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
     EmptyFn k0 = ks->nr == 10 ? gcm_empty_kernel<10> : ks->nr == 12 ? gcm_empty_kernel<12> : gcm_empty_kernel<14>;
     aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k0), kAesSmem);
     if (ast != AES_OK) return ast;
-    k0<<<1, kThreads, kAesSmem, st>>>(kw, ivw[0], ivw[1], ivw[2], d_tag);
+    k0<<<1, kThreads, kAesSmem, st>>>(kw, j0, ivh, d_tag);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM launch");
     return AES_OK;
   }
@@ -528,11 +594,9 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
   g.a = a;
   g.aad_len = aad_len;
   g.len = nbytes;
-  g.iv0 = ivw[0];
-  g.iv1 = ivw[1];
-  g.iv2 = ivw[2];
+  g.j0 = j0;
   g.decrypt = dir == AES_DECRYPT;
-  k<<<nb, kThreads, kMainSmem, st>>>(g, kw, work, d_tag, uint64_t(aad_len) * 8u, uint64_t(nbytes) * 8u);
+  k<<<nb, kThreads, kMainSmem, st>>>(g, kw, ivh, work, d_tag, uint64_t(aad_len) * 8u, uint64_t(nbytes) * 8u);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM launch");
   return AES_OK;
 }

@@ -114,7 +114,7 @@ def test_gcm_argument_checks_before_any_cuda_call(aes):
     lib = aes.lib()
     ks = aes.aes_key_expand(bytes(16))
     kp = ctypes.byref(ks)
-    iv = (ctypes.c_uint8 * 16)()
+    iv = (ctypes.c_uint8 * 300)()
     base = 1 << 40  # never dereferenced
     W = aes.aes_gcm_workspace_bytes()
     assert W >= 256 * 16  # a partial sum per CTA and the finished-CTA ticket
@@ -123,7 +123,7 @@ def test_gcm_argument_checks_before_any_cuda_call(aes):
     def call(iv_len=12, aad=None, aad_len=0, src=base, dst=base, n=64, d=0, t=tag, w=work, wb=W):
         return lib.aes_gcm_crypt(kp, iv, iv_len, aad, aad_len, src, dst, n, d, t, w, wb, None)
 
-    for iv_len in (0, 8, 16):
+    for iv_len in (0, 257):
         assert call(iv_len=iv_len) == aes.AES_EINVAL and "IV" in aes.aes_last_error()
     assert call(wb=W - 16) == aes.AES_EINVAL  # workspace too small
     assert call(w=work + 8) == aes.AES_EINVAL  # workspace misaligned

@@ -1,5 +1,6 @@
 """GPU parity for AES-GCM (the counter-based authenticated mode that Section V of the paper
-names as future work; NIST SP 800-38D with 96-bit IVs) against the oracle's GCM.
+names as future work; NIST SP 800-38D) against the oracle's GCM, with 96-bit IVs and with IVs
+of other lengths (J0 by GHASH of the IV, in the kernel).
 
 Output bytes and tags are compared exactly.  Sizes span one to many CTAs, several positions
 per thread, ragged final blocks of data and AAD, and the empty cases.  At 1 GiB the
@@ -48,6 +49,34 @@ def test_gcm_matches_oracle(aes, orc, cuda, key_bits, nbytes, aad_len):
     assert (host(tag) == want_tag).all()
     back, tag2 = aes.gcm(ct, ks, iv.tobytes(), aad=dev(aad) if aad_len else None, dir="decrypt")
     assert (host(back) == pt).all() and (host(tag2) == want_tag).all()
+
+
+@pytest.mark.parametrize("iv_len", [1, 8, 11, 13, 16, 17, 64, 128, 255, 256])
+@pytest.mark.parametrize("nbytes,aad_len", [(0, 0), (0, 20), (37, 5), (16 * 300_000 + 3, 33)])
+def test_gcm_any_iv_length(aes, orc, cuda, iv_len, nbytes, aad_len):
+    rng = np.random.default_rng(1000 * iv_len + nbytes % 997 + aad_len)
+    key_bits = (128, 192, 256)[iv_len % 3]
+    key = rng.integers(0, 256, key_bits // 8, dtype=np.uint8)
+    iv = rng.integers(0, 256, iv_len, dtype=np.uint8)
+    pt = rng.integers(0, 256, nbytes, dtype=np.uint8)
+    aad = rng.integers(0, 256, aad_len, dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes(), key_bits)
+    want_ct, want_tag = orc.gcm_crypt(key, iv, pt, aad)
+    ct, tag = aes.gcm(dev(pt), ks, iv.tobytes(), aad=dev(aad) if aad_len else None)
+    assert (host(ct) == want_ct).all()
+    assert (host(tag) == want_tag).all()
+    back, tag2 = aes.gcm(ct, ks, iv.tobytes(), aad=dev(aad) if aad_len else None, dir="decrypt")
+    assert (host(back) == pt).all() and (host(tag2) == want_tag).all()
+
+
+def test_gcm_iv_length_limits(aes, cuda):
+    import torch
+
+    ks = aes.aes_key_expand(bytes(16))
+    x = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    for bad in (b"", bytes(257)):
+        with pytest.raises(aes.AesError):
+            aes.gcm(x, ks, bad)
 
 
 def test_gcm_decrypt_of_arbitrary_data_and_in_place(aes, orc, cuda):
