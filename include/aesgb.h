@@ -159,6 +159,17 @@ aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* iv, size_t i
                          size_t aad_len, const void* d_in, void* d_out, size_t nbytes, int dir, uint8_t* d_tag,
                          void* d_work, size_t work_bytes, void* cuda_stream);
 
+/* AES-GCM decryption with the tag check on the device: aes_gcm_crypt with dir = AES_DECRYPT
+ * (same arguments and rules), and *d_ok (device int, int-aligned) receives 1 when the tag
+ * computed from the ciphertext equals the 16 bytes at d_expected_tag (device, any alignment),
+ * else 0; all 16 bytes are compared, with no early exit.  The plaintext is written either way:
+ * use it only when *d_ok is 1.  d_expected_tag and d_ok must not overlap d_out, d_tag, the
+ * workspace or each other; NULL for either is AES_EINVAL.  Same single launch. */
+aes_status aes_gcm_decrypt_verify(const aes_key_schedule* ks, const uint8_t* iv, size_t iv_len, const void* d_aad,
+                                  size_t aad_len, const void* d_in, void* d_out, size_t nbytes,
+                                  const uint8_t* d_expected_tag, int* d_ok, uint8_t* d_tag, void* d_work,
+                                  size_t work_bytes, void* cuda_stream);
+
 /* Equality query on a deterministically encrypted column (the encrypted-database use the
  * paper motivates in Section I): under one key and IV, equal 16-byte records have equal
  * ciphertexts, so the records equal to a query are those whose ciphertext equals the query's

@@ -115,6 +115,7 @@ _SIGS: dict[str, tuple] = {
     "aes_set_auto_choice": (_I, [_I, _I, _I, _I, _I]),
     "aes_gcm_workspace_bytes": (_SZ, []),
     "aes_gcm_crypt": (_I, [_KSP, _U8P, _SZ, _VP, _SZ, _VP, _VP, _SZ, _I, _VP, _VP, _SZ, _VP]),
+    "aes_gcm_decrypt_verify": (_I, [_KSP, _U8P, _SZ, _VP, _SZ, _VP, _VP, _SZ, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "aes_crypt_batched_noalloc": (_I, [_KSP, ctypes.c_uint32, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "aes_keypool_create": (_I, [_SZ, ctypes.POINTER(_VP)]),
     "aes_keypool_load_keys": (_I, [_VP, ctypes.c_uint32, _SZ, _U8P, _I, _VP]),
@@ -302,6 +303,39 @@ def aes_gcm_crypt(ks: aes_key_schedule, iv: bytes, d_aad: int, aad_len: int, d_i
     p, _keep = _bytes_ptr(iv)
     _check(lib().aes_gcm_crypt(ctypes.byref(ks), p, len(iv), d_aad, aad_len, d_in, d_out, nbytes, _dir(dir), d_tag,
                                d_work, work_bytes, _stream_ptr(stream)))
+
+
+def aes_gcm_decrypt_verify(ks: aes_key_schedule, iv: bytes, d_aad: int, aad_len: int, d_in: int, d_out: int,
+                           nbytes: int, d_expected_tag: int, d_ok: int, d_tag: int, d_work: int, work_bytes: int,
+                           stream=None) -> None:
+    p, _keep = _bytes_ptr(iv)
+    _check(lib().aes_gcm_decrypt_verify(ctypes.byref(ks), p, len(iv), d_aad, aad_len, d_in, d_out, nbytes,
+                                        d_expected_tag, d_ok, d_tag, d_work, work_bytes, _stream_ptr(stream)))
+
+
+def gcm_open(x, ks: aes_key_schedule, iv: bytes, tag, aad=None, out=None, stream=None):
+    """AES-GCM decryption of the CUDA uint8 tensor x with the received 16-byte `tag` (CUDA
+    tensor) checked on the device; returns (plaintext, ok) with ok a CUDA int32 tensor holding
+    1 if the tag matched, else 0.  Use the plaintext only when ok is 1."""
+    import torch
+
+    if x.dtype != torch.uint8 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA uint8 tensor")
+    if tag.dtype != torch.uint8 or not tag.is_cuda or tag.numel() != 16:
+        raise ValueError("tag must be 16 bytes in a CUDA uint8 tensor")
+    if out is None:
+        out = torch.empty_like(x)
+    ok = torch.empty(1, dtype=torch.int32, device=x.device)
+    computed = torch.empty(16, dtype=torch.uint8, device=x.device)
+    work = torch.empty(aes_gcm_workspace_bytes(), dtype=torch.uint8, device=x.device)
+    a_ptr, a_len = (aad.data_ptr(), aad.numel()) if aad is not None and aad.numel() else (None, 0)
+    aes_gcm_decrypt_verify(ks, iv, a_ptr, a_len, x.data_ptr() if x.numel() else None,
+                           out.data_ptr() if x.numel() else None, x.numel(), tag.data_ptr(), ok.data_ptr(),
+                           computed.data_ptr(), work.data_ptr(), work.numel(), stream)
+    if isinstance(stream, torch.cuda.Stream):  # the scratch tensors are freed here, still in use there
+        for t in (work, computed):
+            t.record_stream(stream)
+    return out, ok
 
 
 def gcm(x, ks: aes_key_schedule, iv: bytes, aad=None, dir="encrypt", out=None, stream=None):

@@ -235,7 +235,23 @@ struct GcmArgs {
   uint32_t K;        // positions per thread
   uint4 j0;          // J0 of a 96-bit IV (IV || 0^31 || 1); ignored when IvHash::n > 0
   int decrypt;
+  const uint8_t* expect;  // expected tag (decryption with verification), or nullptr
+  int* ok;                // receives 1 if the computed tag equals *expect, else 0
 };
+
+// Writes the tag tg (little-endian words) to tag[0..15]; with an expected tag, also *ok = 1 if
+// every byte matches, else 0 (all 16 bytes compared, no early exit).
+__device__ void put_tag(uint4 tg, uint8_t* tag, const uint8_t* expect, int* ok) {
+  const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
+  uint32_t diff = 0;
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    const uint8_t v = uint8_t(tw[b >> 2] >> (8 * (b & 3)));
+    tag[b] = v;
+    if (expect) diff |= uint32_t(v ^ expect[b]);
+  }
+  if (expect) *ok = diff == 0u ? 1 : 0;
+}
 
 // For an IV other than 96 bits: the blocks GHASH runs over to give J0 (the IV zero-padded to
 // whole blocks, then 0^64 and the IV's bit length), as little-endian words; n = 0 means that
@@ -463,10 +479,7 @@ gcm_kernel(const GcmArgs g, const KeyWords kw, const IvHash ivh, char* work, uin
       const uint4 L = make_uint4(bswap32(uint32_t(abits >> 32)), bswap32(uint32_t(abits)), bswap32(uint32_t(cbits >> 32)),
                                  bswap32(uint32_t(cbits)));
       const uint4 S = mul_tab(xor4(gsum, L), h_tab);
-      const uint4 tg = xor4(s_he[1], S);
-      const uint32_t tw[4] = {tg.x, tg.y, tg.z, tg.w};
-#pragma unroll
-      for (int b = 0; b < 16; ++b) tag[b] = uint8_t(tw[b >> 2] >> (8 * (b & 3)));
+      put_tag(xor4(s_he[1], S), tag, g.expect, g.ok);
       *reinterpret_cast<unsigned*>(work + kCounter) = 0u;  // ready for the next call on this workspace
     }
   }
@@ -476,7 +489,7 @@ gcm_kernel(const GcmArgs g, const KeyWords kw, const IvHash ivh, char* work, uin
 // i.e. Cipher(J0).  One warp (J0 by GHASH for an IV other than 96 bits), one thread writes.
 template <int NR>
 __global__ void __launch_bounds__(kThreads, 1) gcm_empty_kernel(const KeyWords kw, const uint4 j0_direct, const IvHash ivh,
-                                                               uint8_t* tag) {
+                                                               uint8_t* tag, const uint8_t* expect, int* ok) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ Be s_hmx[128];
   fill_tables<AES_ENCRYPT>(smem);
@@ -486,17 +499,13 @@ __global__ void __launch_bounds__(kThreads, 1) gcm_empty_kernel(const KeyWords k
     const uint32_t lc = (threadIdx.x & 31u) * 4u;
     uint4 j0 = j0_direct;
     if (ivh.n) j0 = j0_from_iv(ivh, to_be(crypt_block<NR, AES_ENCRYPT>(make_uint4(0, 0, 0, 0), kw, sm, lc)), s_hmx);
-    if (threadIdx.x == 0) {
-      const uint4 e = crypt_block<NR, AES_ENCRYPT>(j0, kw, sm, lc);
-      const uint32_t tw[4] = {e.x, e.y, e.z, e.w};
-      for (int b = 0; b < 16; ++b) tag[b] = uint8_t(tw[b >> 2] >> (8 * (b & 3)));
-    }
+    if (threadIdx.x == 0) put_tag(crypt_block<NR, AES_ENCRYPT>(j0, kw, sm, lc), tag, expect, ok);
   }
 }
 
 constexpr int kUnroll = 2;
 using GcmFn = void (*)(const GcmArgs, const KeyWords, const IvHash, char*, uint8_t*, uint64_t, uint64_t);
-using EmptyFn = void (*)(const KeyWords, const uint4, const IvHash, uint8_t*);
+using EmptyFn = void (*)(const KeyWords, const uint4, const IvHash, uint8_t*, const uint8_t*, int*);
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
@@ -510,10 +519,11 @@ using namespace aesgb;
 
 extern "C" size_t aes_gcm_workspace_bytes(void) { return kWorkBytes; }
 
-extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* iv, size_t iv_len, const void* d_aad,
-                                    size_t aad_len, const void* d_in, void* d_out, size_t nbytes, int dir, uint8_t* d_tag,
-                                    void* d_work, size_t work_bytes, void* cuda_stream) {
-  clear_error();
+namespace {
+
+aes_status gcm_launch(const aes_key_schedule* ks, const uint8_t* iv, size_t iv_len, const void* d_aad, size_t aad_len,
+                      const void* d_in, void* d_out, size_t nbytes, int dir, uint8_t* d_tag, const uint8_t* d_expect,
+                      int* d_ok, void* d_work, size_t work_bytes, void* cuda_stream) {
   if (!schedule_ok(ks)) return set_error(AES_EINVAL, "invalid key schedule (nr must be 10, 12 or 14)");
   if (dir != AES_ENCRYPT && dir != AES_DECRYPT) return set_error(AES_EINVAL, "dir must be AES_ENCRYPT or AES_DECRYPT");
   if (!iv || iv_len == 0 || iv_len > size_t(kMaxIvBytes))
@@ -534,6 +544,11 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
   if (overlaps(d_work, kWorkBytes, d_in, nbytes) || overlaps(d_work, kWorkBytes, d_out, nbytes) ||
       overlaps(d_work, kWorkBytes, d_aad, aad_len) || overlaps(d_work, kWorkBytes, d_tag, 16))
     return set_error(AES_EINVAL, "workspace overlaps a buffer");
+  if (d_expect && (overlaps(d_expect, 16, d_out, nbytes) || overlaps(d_expect, 16, d_tag, 16) ||
+                   overlaps(d_expect, 16, d_work, kWorkBytes) || overlaps(d_ok, sizeof(int), d_out, nbytes) ||
+                   overlaps(d_ok, sizeof(int), d_tag, 16) || overlaps(d_ok, sizeof(int), d_work, kWorkBytes) ||
+                   overlaps(d_ok, sizeof(int), d_expect, 16)))
+    return set_error(AES_EINVAL, "expected tag or verdict overlaps a buffer the call writes");
   const DeviceInfo* di = current_device_info();
   if (!di) return AES_ECUDA;
   if (di->smem_optin < int(kMainSmem)) return set_error(AES_EINVAL, "device has too little shared memory for GCM");
@@ -574,7 +589,7 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
     EmptyFn k0 = ks->nr == 10 ? gcm_empty_kernel<10> : ks->nr == 12 ? gcm_empty_kernel<12> : gcm_empty_kernel<14>;
     aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k0), kAesSmem);
     if (ast != AES_OK) return ast;
-    k0<<<1, kThreads, kAesSmem, st>>>(kw, j0, ivh, d_tag);
+    k0<<<1, kThreads, kAesSmem, st>>>(kw, j0, ivh, d_tag, d_expect, d_ok);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM launch");
     return AES_OK;
   }
@@ -596,7 +611,30 @@ extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* i
   g.len = nbytes;
   g.j0 = j0;
   g.decrypt = dir == AES_DECRYPT;
+  g.expect = d_expect;
+  g.ok = d_ok;
   k<<<nb, kThreads, kMainSmem, st>>>(g, kw, ivh, work, d_tag, uint64_t(aad_len) * 8u, uint64_t(nbytes) * 8u);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "GCM launch");
   return AES_OK;
+}
+
+}  // namespace
+
+extern "C" aes_status aes_gcm_crypt(const aes_key_schedule* ks, const uint8_t* iv, size_t iv_len, const void* d_aad,
+                                    size_t aad_len, const void* d_in, void* d_out, size_t nbytes, int dir, uint8_t* d_tag,
+                                    void* d_work, size_t work_bytes, void* cuda_stream) {
+  clear_error();
+  return gcm_launch(ks, iv, iv_len, d_aad, aad_len, d_in, d_out, nbytes, dir, d_tag, nullptr, nullptr, d_work, work_bytes,
+                    cuda_stream);
+}
+
+extern "C" aes_status aes_gcm_decrypt_verify(const aes_key_schedule* ks, const uint8_t* iv, size_t iv_len,
+                                             const void* d_aad, size_t aad_len, const void* d_in, void* d_out,
+                                             size_t nbytes, const uint8_t* d_expected_tag, int* d_ok, uint8_t* d_tag,
+                                             void* d_work, size_t work_bytes, void* cuda_stream) {
+  clear_error();
+  if (!d_expected_tag || !d_ok) return set_error(AES_EINVAL, "null expected tag or verdict");
+  if (reinterpret_cast<uintptr_t>(d_ok) & (alignof(int) - 1)) return set_error(AES_EINVAL, "verdict must be int-aligned");
+  return gcm_launch(ks, iv, iv_len, d_aad, aad_len, d_in, d_out, nbytes, AES_DECRYPT, d_tag, d_expected_tag, d_ok, d_work,
+                    work_bytes, cuda_stream);
 }

@@ -69,6 +69,40 @@ def test_gcm_any_iv_length(aes, orc, cuda, iv_len, nbytes, aad_len):
     assert (host(back) == pt).all() and (host(tag2) == want_tag).all()
 
 
+@pytest.mark.parametrize("iv_len,nbytes,aad_len", [(12, 16 * 50_000 + 5, 21), (12, 0, 0), (20, 100, 0), (7, 0, 9)])
+def test_gcm_open_checks_the_tag_on_the_device(aes, orc, cuda, iv_len, nbytes, aad_len):
+    rng = np.random.default_rng(77 + iv_len + nbytes)
+    key = rng.integers(0, 256, 16, dtype=np.uint8)
+    iv = rng.integers(0, 256, iv_len, dtype=np.uint8).tobytes()
+    pt = rng.integers(0, 256, nbytes, dtype=np.uint8)
+    aad = rng.integers(0, 256, aad_len, dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes())
+    ct, tag = orc.gcm_crypt(key, iv, pt, aad)
+    d_aad = dev(aad) if aad_len else None
+    out, ok = aes.gcm_open(dev(ct), ks, iv, dev(tag), aad=d_aad)
+    assert int(host(ok)[0]) == 1 and (host(out) == pt).all()
+    # any wrong tag byte, ciphertext bit or AAD byte fails the check
+    for b in (0, 7, 15):
+        bad = tag.copy()
+        bad[b] ^= 0x40
+        _, ok = aes.gcm_open(dev(ct), ks, iv, dev(bad), aad=d_aad)
+        assert int(host(ok)[0]) == 0, b
+    if nbytes:
+        ct2 = ct.copy()
+        ct2[nbytes // 2] ^= 1
+        _, ok = aes.gcm_open(dev(ct2), ks, iv, dev(tag), aad=d_aad)
+        assert int(host(ok)[0]) == 0
+    if aad_len:
+        aad2 = aad.copy()
+        aad2[0] ^= 0x80
+        _, ok = aes.gcm_open(dev(ct), ks, iv, dev(tag), aad=dev(aad2))
+        assert int(host(ok)[0]) == 0
+    # in place
+    x = dev(ct)
+    _, ok = aes.gcm_open(x, ks, iv, dev(tag), aad=d_aad, out=x)
+    assert int(host(ok)[0]) == 1 and (host(x) == pt).all()
+
+
 def test_gcm_iv_length_limits(aes, cuda):
     import torch
 
