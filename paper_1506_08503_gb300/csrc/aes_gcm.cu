@@ -548,7 +548,7 @@ aes_status gcm_launch(const aes_key_schedule* ks, const uint8_t* iv, size_t iv_l
                    overlaps(d_expect, 16, d_work, kWorkBytes) || overlaps(d_ok, sizeof(int), d_out, nbytes) ||
                    overlaps(d_ok, sizeof(int), d_tag, 16) || overlaps(d_ok, sizeof(int), d_work, kWorkBytes) ||
                    overlaps(d_ok, sizeof(int), d_expect, 16)))
-    return set_error(AES_EINVAL, "expected tag or verdict overlaps a buffer the call writes");
+    return set_error(AES_EINVAL, "expected tag or ok flag overlaps a buffer the call writes");
   const DeviceInfo* di = current_device_info();
   if (!di) return AES_ECUDA;
   if (di->smem_optin < int(kMainSmem)) return set_error(AES_EINVAL, "device has too little shared memory for GCM");
@@ -633,8 +633,8 @@ extern "C" aes_status aes_gcm_decrypt_verify(const aes_key_schedule* ks, const u
                                              size_t nbytes, const uint8_t* d_expected_tag, int* d_ok, uint8_t* d_tag,
                                              void* d_work, size_t work_bytes, void* cuda_stream) {
   clear_error();
-  if (!d_expected_tag || !d_ok) return set_error(AES_EINVAL, "null expected tag or verdict");
-  if (reinterpret_cast<uintptr_t>(d_ok) & (alignof(int) - 1)) return set_error(AES_EINVAL, "verdict must be int-aligned");
+  if (!d_expected_tag || !d_ok) return set_error(AES_EINVAL, "null expected tag or ok flag");
+  if (reinterpret_cast<uintptr_t>(d_ok) & (alignof(int) - 1)) return set_error(AES_EINVAL, "ok flag must be int-aligned");
   return gcm_launch(ks, iv, iv_len, d_aad, aad_len, d_in, d_out, nbytes, AES_DECRYPT, d_tag, d_expected_tag, d_ok, d_work,
                     work_bytes, cuda_stream);
 }

@@ -134,7 +134,7 @@ def test_gcm_argument_checks_before_any_cuda_call(aes):
     assert call(dst=base + 16) == aes.AES_EINVAL  # partial overlap
     assert call(aad=None, aad_len=5) == aes.AES_EINVAL
 
-    # decryption with the tag check: the expected tag and the verdict are required and must not
+    # decryption with the tag check: the expected tag and the ok flag are required and must not
     # overlap what the call writes
     lib.aes_gcm_decrypt_verify.restype = ctypes.c_int
     exp_tag, ok = base + (1 << 32), base + (1 << 33)
@@ -144,10 +144,10 @@ def test_gcm_argument_checks_before_any_cuda_call(aes):
 
     assert verify(e=None) == aes.AES_EINVAL and "expected tag" in aes.aes_last_error()
     assert verify(o=None) == aes.AES_EINVAL
-    assert verify(o=ok + 2) == aes.AES_EINVAL  # verdict not int-aligned
-    assert verify(o=tag + 4) == aes.AES_EINVAL  # verdict inside the tag
+    assert verify(o=ok + 2) == aes.AES_EINVAL  # ok flag not int-aligned
+    assert verify(o=tag + 4) == aes.AES_EINVAL  # ok flag inside the tag
     assert verify(e=base + 16) == aes.AES_EINVAL  # expected tag inside the output
-    assert verify(o=work + 64) == aes.AES_EINVAL  # verdict inside the workspace
+    assert verify(o=work + 64) == aes.AES_EINVAL  # ok flag inside the workspace
     assert call(aad=base + 48, aad_len=32) == aes.AES_EINVAL  # output overlaps the AAD
     assert call(n=16 * (1 << 32)) == aes.AES_EINVAL  # beyond 2^32 - 2 blocks
     assert call(src=None, dst=None) == aes.AES_EINVAL
