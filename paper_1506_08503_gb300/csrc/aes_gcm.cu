@@ -1,8 +1,9 @@
-// aes_gcm.cu -- AES-GCM (Galois/Counter Mode, NIST SP 800-38D) with 96-bit IVs.
+// aes_gcm.cu -- AES-GCM (Galois/Counter Mode, NIST SP 800-38D).
 //
 // Section V of the paper names counter-based authenticated modes (GCM) as future work.  GCM
-// encrypts like counter mode -- data block j is XORed with the cipher of J0 = IV || 0^31 || 1
-// whose last 32 bits are replaced by 2 + j mod 2^32 -- and authenticates with GHASH, a
+// encrypts like counter mode -- data block j is XORed with the cipher of J0 (IV || 0^31 || 1
+// for a 96-bit IV, else the GHASH of the padded IV and its length) whose last 32 bits are
+// increased by 1 + j mod 2^32 -- and authenticates with GHASH, a
 // polynomial in H = Cipher(0^128) over GF(2^128) modulo x^128 + x^7 + x^2 + x + 1:
 //     S = X_1 H^m + X_2 H^(m-1) + ... + X_m H,    tag = Cipher(J0) + S,
 // where X runs over the AAD and the ciphertext (each zero-padded to whole blocks) and a last
@@ -15,8 +16,8 @@
 // Q = H^T, giving Y_t = sum_k X_(t+kT) Q^(K-1-k).  Then
 //     sum_i X_i H^(n-i) = H * sum_t Y_t H^(T-1-t),
 // and the last sum is a binary tree whose level j multiplies by H^(2^j): five levels between
-// the lanes of a warp (shuffles), four between the 16 warps of a CTA, eight between up to
-// 256 CTAs (in a final one-CTA kernel).
+// the lanes of a warp (shuffles), four between the 16 warps of a CTA, and between the CTAs
+// as many as their count needs (none for one CTA, up to eight), in the CTA that finishes last.
 //
 // Multiplication by a fixed element M is linear, so it is one table lookup per 4-bit nibble
 // of the other operand: Y * M = XOR over the 32 nibbles j of T_j[nibble_j(Y)], with
@@ -196,9 +197,9 @@ __device__ __forceinline__ uint4 shfl_down4(uint4 v, int d) {
 __device__ __forceinline__ uint4 lane_tree(uint4 v, const uint4* tabs, int levels) {
   const uint32_t lane = threadIdx.x & 31u;
   for (int j = 0; j < levels; ++j) {
-    const uint4 o = shfl_down4(v, 1 << j);
-    const uint4 m = mul_tab(v, tabs + j * 512);
-    if ((lane & ((2u << j) - 1u)) == 0) v = xor4(m, o);
+    const uint4 o = shfl_down4(v, 1 << j);  // every lane takes part in the shuffle
+    // only the lanes that keep a sum multiply: fewer lanes issue table loads at each level
+    if ((lane & ((2u << j) - 1u)) == 0) v = xor4(mul_tab(v, tabs + j * 512), o);
   }
   return v;
 }
@@ -331,9 +332,12 @@ gcm_kernel(const GcmArgs g, const KeyWords kw, const IvHash ivh, char* work, uin
   }
   const uint4 j0 = s_j0;
   if (tid == 0) {
+    // H^(2^j) for j <= 9 + LV, LV the last CTA's tree levels (2^LV >= gridDim.x): the in-CTA
+    // tree takes j < 9, Q = H^T (T = 512 gridDim.x) its bits up to 9 + LV, the last tree 9 .. 8 + LV
+    const int LV = gridDim.x > 1 ? 32 - __clz(gridDim.x - 1u) : 0;
     Be p = to_be(s_he[0]);
     s_pow[0] = p;
-    for (int j = 1; j < 18; ++j) s_pow[j] = p = square(p);
+    for (int j = 1; j <= 9 + LV; ++j) s_pow[j] = p = square(p);
   }
   __syncthreads();
   // Q = H^T (T = gridDim.x * 512 < 2^18) from the multiples of the factors H^(2^b), kept in
@@ -458,23 +462,34 @@ gcm_kernel(const GcmArgs g, const KeyWords kw, const IvHash ivh, char* work, uin
   if (!s_last) return;  // CTA-uniform; no barrier follows in the other CTAs
   __threadfence();
 
-  // The last CTA: CTA b's partial at slot 256 - nb + b carries (H^512)^(255 - slot); a tree
-  // over the 256 slots with the tables of H^(2^9) .. H^(2^16), then the tag.
-  if (tid < 8) s_ms[tid] = s_pow[9 + tid];
-  if (tid == 8) s_ms[8] = s_pow[0];
-  __syncthreads();
-  build_tables(s_ms, 9, mx, tabs);  // tabs[0..7]: H^(2^9..2^16), tabs[8]: H
+  // The last CTA: with LV levels (2^LV >= nb slots), CTA b's partial at slot 2^LV - nb + b
+  // carries (H^512)^(2^LV - 1 - slot); a tree over the slots with the tables of H^(2^9) ..
+  // H^(2^(8+LV)) (lanes of a warp for the first five levels, then the warps' sums), then the
+  // tag.  A single CTA (LV = 0) needs no tree.
   const uint32_t nb = gridDim.x;
+  const int LV = nb > 1 ? 32 - __clz(nb - 1u) : 0;
+  const uint32_t S = 1u << LV;
+  if (tid < uint32_t(LV)) s_ms[tid] = s_pow[9 + tid];
+  if (tid == uint32_t(LV)) s_ms[LV] = s_pow[0];
+  __syncthreads();
+  build_tables(s_ms, LV + 1, mx, tabs);  // tabs[0..LV-1]: H^(2^9..2^(8+LV)), tabs[LV]: H
+  const int l1 = LV < 5 ? LV : 5;
+  const uint32_t lanes = S < 32u ? 32u : S;  // whole warps take part in the shuffles
   uint4 v = make_uint4(0, 0, 0, 0);
-  if (tid < kMaxCtas && tid >= kMaxCtas - nb) v = __ldcg(reinterpret_cast<const uint4*>(work + kParts) + (tid - (kMaxCtas - nb)));
-  if (tid < kMaxCtas) v = lane_tree(v, tabs, 5);
-  if (tid < kMaxCtas && lane == 0) s_warp[tid >> 5] = v;
+  if (tid < S && tid >= S - nb) v = __ldcg(reinterpret_cast<const uint4*>(work + kParts) + (tid - (S - nb)));
+  if (tid < lanes) {
+    v = lane_tree(v, tabs, l1);
+    if (lane == 0) s_warp[tid >> 5] = v;
+  }
   __syncthreads();
   if (tid < 32) {
-    uint4 w = lane < kMaxCtas / 32 ? s_warp[lane] : make_uint4(0, 0, 0, 0);
-    w = lane_tree(w, tabs + 5 * 512, 3);
+    uint4 w = s_warp[0];
+    if (LV > 5) {
+      w = lane < (S >> 5) ? s_warp[lane] : make_uint4(0, 0, 0, 0);
+      w = lane_tree(w, tabs + 5 * 512, LV - 5);
+    }
     if (lane == 0) {
-      const uint4* h_tab = tabs + 8 * 512;
+      const uint4* h_tab = tabs + LV * 512;
       const uint4 gsum = mul_tab(w, h_tab);  // sum_i X_i H^(n - i)
       const uint4 L = make_uint4(bswap32(uint32_t(abits >> 32)), bswap32(uint32_t(abits)), bswap32(uint32_t(cbits >> 32)),
                                  bswap32(uint32_t(cbits)));

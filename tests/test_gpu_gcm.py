@@ -103,6 +103,23 @@ def test_gcm_open_checks_the_tag_on_the_device(aes, orc, cuda, iv_len, nbytes, a
     assert int(host(ok)[0]) == 1 and (host(x) == pt).all()
 
 
+@pytest.mark.parametrize("nb", [1, 2, 3, 31, 32, 33, 64, 65, 128, 129, 152])
+def test_gcm_every_cross_cta_tree_depth(aes, orc, cuda, nb):
+    """The CTA that finishes last combines the CTAs' partial sums with a tree of as many levels
+    as the CTA count needs (none for one CTA, up to eight): hashed-block counts that give each
+    count of CTAs (512 positions per CTA) around the powers of two."""
+    n = 512 * (nb - 1) + 1 + (nb % 7) * 11
+    rng = np.random.default_rng(500 + nb)
+    key = rng.integers(0, 256, 16, dtype=np.uint8)
+    iv = rng.integers(0, 256, 12, dtype=np.uint8)
+    pt = rng.integers(0, 256, 16 * (n - 1) + 5, dtype=np.uint8)  # n blocks, the last ragged
+    ks = aes.aes_key_expand(key.tobytes())
+    want_ct, want_tag = orc.gcm_crypt(key, iv, pt)
+    ct, tag = aes.gcm(dev(pt), ks, iv.tobytes())
+    assert (host(tag) == want_tag).all()
+    assert (host(ct) == want_ct).all()
+
+
 def test_gcm_iv_length_limits(aes, cuda):
     import torch
 
