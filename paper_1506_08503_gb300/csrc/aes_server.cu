@@ -8,12 +8,14 @@
 //   host payloads that the kernel can reach itself (a device with direct access to host
 //   memory, 16-byte aligned buffers) are read and written in place; other host-sourced
 //   payloads are copied into the staging arena (or straight into a device destination), the
-//   batch graph runs the cipher, and other host destinations are copied back; a host callback at the end of the stream marks the batch's
-//   requests complete, frees their staging and wakes the thread and any waiting poll.
+//   batch graph runs the cipher, and other host destinations are copied back; an event at
+//   the end of the stream marks the batch done, and the server's thread, which polls the
+//   events of its batches in flight, then marks the batch's requests complete, frees their
+//   staging and wakes any waiting poll.
 // Requests arriving while batches run are admitted into the next free stream's batch, so the
 // device works on several batches at once and nobody waits for a full drain.
 //
-// Threads: the worker only admits (under the server mutex); each stream slot has an issuer
+// Threads: the worker admits (under the server mutex) and retires; each stream slot has an issuer
 // thread that builds the admitted batch's descriptors and launches it, so the host work of
 // several batches (linear in their request counts) proceeds in parallel.  A bulk submission
 // reserves all its tickets at once and writes them in chunks, so admission starts before the
@@ -28,6 +30,7 @@
 #include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -110,13 +113,13 @@ struct StreamSlot {
   bool pending = false;      // admitted, waiting for this slot's issuer thread
   bool inject_fail = false;  // fault injection: the issuer fails this batch
   uint64_t first = 0, last = 0;  // the batch is the ticket range [first, last)
+  cudaEvent_t done_ev = nullptr;  // recorded after the batch's last operation on the stream
+  std::atomic<bool> awaiting{false};  // issued: the worker polls done_ev and retires the batch
+  StreamSlot() = default;
+  StreamSlot(const StreamSlot&) = delete;
+  StreamSlot& operator=(const StreamSlot&) = delete;
   std::vector<double> lat;   // retirement scratch (max_batch entries)
   std::vector<std::pair<size_t, size_t>> frees;
-};
-
-struct DoneMsg {
-  struct aes_server* s;
-  int slot;
 };
 
 
@@ -129,8 +132,7 @@ struct aes_server {
   uint8_t* arena_base = nullptr;
   Arena arena;
   bool host_direct = false;  // kernels may load and store host memory (see DeviceInfo)
-  std::vector<StreamSlot> slots;
-  std::vector<DoneMsg> done_msgs;
+  std::deque<StreamSlot> slots;  // a deque: the slots hold atomics and are never moved
 
   std::mutex mu;
   std::condition_variable cv_work, cv_done, cv_issue;
@@ -217,15 +219,8 @@ void retire(aes_server* s, StreamSlot& sl, double t, int state) {
   s->cv_work.notify_one();
 }
 
-// Runs on a CUDA driver thread once everything queued for the batch has finished (no CUDA
-// calls here).
-void CUDART_CB on_batch_done(void* p) {
-  DoneMsg* m = static_cast<DoneMsg*>(p);
-  retire(m->s, m->s->slots[m->slot], now_s(), AES_REQ_DONE);
-}
-
 // Issues the tickets [sl.first, sl.last) on slot i (mu NOT held; the batch owns its ring
-// slots until its callback retires them).
+// slots until the worker sees its done event and retires them).
 aes_status issue(aes_server* s, int i) {
   StreamSlot& sl = s->slots[i];
   cudaStream_t st = sl.stream;
@@ -267,8 +262,38 @@ aes_status issue(aes_server* s, int i) {
       if ((e = cudaMemcpyAsync(q.r.dst, s->arena_base + q.stage_off, q.r.length, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_error(e, "D2H");
   }
-  if ((e = cudaLaunchHostFunc(st, on_batch_done, &s->done_msgs[i])) != cudaSuccess) return cuda_error(e, "cudaLaunchHostFunc");
+  if ((e = cudaEventRecord(sl.done_ev, st)) != cudaSuccess) return cuda_error(e, "cudaEventRecord(batch done)");
   return AES_OK;
+}
+
+// A slot's batch has been issued: the worker polls its done event from now on.  Called with
+// mu held, so the worker, which checks the flags under mu before it sleeps, cannot miss it.
+void mark_issued(aes_server* s, StreamSlot& sl) {
+  sl.awaiting.store(true, std::memory_order_release);
+  s->cv_work.notify_one();
+}
+
+bool any_awaiting(const aes_server* s) {
+  for (const StreamSlot& sl : s->slots)
+    if (sl.awaiting.load(std::memory_order_acquire)) return true;
+  return false;
+}
+
+// Retires every issued batch whose done event has fired (mu NOT held: the event queries do
+// not block the submitters and pollers).  Returns whether a batch is still in flight.
+bool poll_completions(aes_server* s) {
+  bool in_flight = false;
+  for (StreamSlot& sl : s->slots) {
+    if (!sl.awaiting.load(std::memory_order_acquire)) continue;
+    const cudaError_t q = cudaEventQuery(sl.done_ev);
+    if (q == cudaErrorNotReady) {
+      in_flight = true;
+      continue;
+    }
+    sl.awaiting.store(false, std::memory_order_relaxed);
+    retire(s, sl, now_s(), q == cudaSuccess ? AES_REQ_DONE : AES_REQ_FAILED);
+  }
+  return in_flight;
 }
 
 // One thread per stream slot builds and launches the slot's batches, so that the descriptor
@@ -289,15 +314,32 @@ void issuer_main(aes_server* s, int i) {
       retire(s, sl, now_s(), AES_REQ_FAILED);
     }
     lk.lock();
+    if (rc == AES_OK) mark_issued(s, sl);
   }
 }
 
 constexpr uint64_t kInlineIssue = 256;  // batches up to this many requests skip the hand-off
 
+// The worker admits queued requests into batches and retires finished batches.  While a
+// batch is in flight it does not sleep: it polls the batches' done events between admissions
+// (yielding the core between rounds), so a batch is retired as soon as the GPU has finished
+// it; with nothing in flight it sleeps on cv_work.
 void worker_main(aes_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
+  auto idle = [&](bool in_flight) {
+    if (in_flight || any_awaiting(s)) {
+      lk.unlock();
+      std::this_thread::yield();
+      lk.lock();
+    } else {
+      s->cv_work.wait(lk);
+    }
+  };
   for (;;) {
+    lk.unlock();
+    const bool in_flight = poll_completions(s);
+    lk.lock();
     bool any_busy = false;
     int free_slot = -1;
     for (size_t i = 0; i < s->slots.size(); ++i) {
@@ -312,11 +354,11 @@ void worker_main(aes_server* s) {
       }
       s->cv_done.notify_all();
       if (!any_busy) break;
-      s->cv_work.wait(lk);
+      idle(in_flight);
       continue;
     }
     if (free_slot < 0 || s->admit == s->filled) {
-      s->cv_work.wait(lk);
+      idle(in_flight);
       continue;
     }
     // 2. admit from the head of the queue into one batch: the ticket range [admit, t)
@@ -335,7 +377,8 @@ void worker_main(aes_server* s) {
       ++t;
     }
     if (t == first) {
-      if (!any_busy) s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+      if (in_flight || any_awaiting(s)) idle(true);
+      else if (!any_busy) s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
       else s->cv_work.wait(lk);
       continue;
     }
@@ -358,6 +401,7 @@ void worker_main(aes_server* s) {
         retire(s, sl, now_s(), AES_REQ_FAILED);
       }
       lk.lock();
+      if (rc == AES_OK) sl.awaiting.store(true, std::memory_order_release);
     } else {
       sl.pending = true;
       s->cv_issue.notify_all();
@@ -459,6 +503,7 @@ aes_status aes_server_destroy(aes_server* s) {
   for (StreamSlot& sl : s->slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     if (sl.batch) aes_batch_destroy(sl.batch);
+    if (sl.done_ev) cudaEventDestroy(sl.done_ev);
     if (sl.stream) cudaStreamDestroy(sl.stream);
   }
   if (s->arena_base) cudaFree(s->arena_base);
@@ -511,8 +556,8 @@ aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_s
   }
   s->mask = ring - 1;
   s->ring_size = ring;
-  s->slots.resize(cfg->nstreams);
   try {
+    for (uint32_t i = 0; i < cfg->nstreams; ++i) s->slots.emplace_back();
     for (StreamSlot& sl : s->slots) {
       sl.lat.reserve(cfg->max_batch);
       sl.frees.reserve(cfg->max_batch);
@@ -521,12 +566,14 @@ aes_status aes_server_create(const aes_server_cfg* cfg, aes_keypool* pool, aes_s
     aes_server_destroy(s);
     return set_error(AES_ENOMEM, "host allocation failed");
   }
-  s->done_msgs.resize(cfg->nstreams);
   for (uint32_t i = 0; i < cfg->nstreams; ++i) {
-    s->done_msgs[i] = DoneMsg{s, int(i)};
     if ((e = cudaStreamCreateWithFlags(&s->slots[i].stream, cudaStreamNonBlocking)) != cudaSuccess) {
       aes_server_destroy(s);
       return cuda_error(e, "cudaStreamCreate");
+    }
+    if ((e = cudaEventCreateWithFlags(&s->slots[i].done_ev, cudaEventDisableTiming)) != cudaSuccess) {
+      aes_server_destroy(s);
+      return cuda_error(e, "cudaEventCreate");
     }
     aes_status st = aes_batch_create(pool, cfg->max_batch, &s->slots[i].batch);
     if (st != AES_OK) {
