@@ -231,3 +231,41 @@ def test_submit_many_is_all_or_nothing(aes_lib_ready, orc):
             assert (got[o:o + L] == f(keys[int(reqs[i]["key_idx"])], data[o:o + L], threads=THREADS)).all(), i
         st = srv.stats()
         assert st["completed"] == n and st["mean_batch"] > 2
+
+
+def test_trickled_requests_all_complete_without_a_lost_wakeup(aes_lib_ready, orc):
+    """Requests submitted one at a time with irregular gaps (from none to a few hundred
+    microseconds), so that the server's thread keeps switching between sleeping (nothing in
+    flight) and polling its batches' done events: every request completes within a bounded
+    wait, with the oracle's bytes."""
+    import torch
+
+    rng = np.random.default_rng(43)
+    pool, keys = make_pool(rng)
+    n = 1500
+    lengths = 16 * rng.integers(1, 300, n)
+    offs = np.concatenate([[0], np.cumsum(lengths)[:-1]])
+    data = rng.integers(0, 256, int(lengths.sum()), dtype=np.uint8)
+    src = torch.from_numpy(data).cuda()
+    dst = torch.empty_like(src)
+    kidx = rng.integers(0, 8, n)
+    dirs = rng.integers(0, 2, n)
+    gaps = rng.choice([0.0, 0.0, 20e-6, 200e-6], n)
+    with pool, aes.Server(pool, hbm_budget=64 << 20, nstreams=4, max_batch=64) as srv:
+        tickets = []
+        for i in range(n):
+            if gaps[i]:
+                end = time.perf_counter() + gaps[i]
+                while time.perf_counter() < end:
+                    pass
+            o = int(offs[i])
+            tickets.append(srv.submit(int(kidx[i]), int(dirs[i]), src.data_ptr() + o, dst.data_ptr() + o,
+                                      int(lengths[i]), True, True))
+        for t in tickets:
+            assert srv.poll(t, timeout_us=5_000_000) == aes.AES_REQ_DONE
+        st = srv.stats()
+        assert st["completed"] == n and st["failed"] == 0
+    got = dst.cpu().numpy()
+    for i in rng.choice(n, 60, replace=False):
+        o, L = int(offs[i]), int(lengths[i])
+        assert (got[o:o + L] == oracle_crypt(orc, keys[int(kidx[i])], data[o:o + L], int(dirs[i]))).all(), i
