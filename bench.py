@@ -70,6 +70,8 @@ def roofline_peak_gbs(sms: int, mhz: float) -> float:
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--probe", choices=["pipes", "corun", "host-link"], default=None,
+                   help="run one measurement probe behind the roofline or a design note, print its JSON, exit")
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -795,8 +797,128 @@ def run_ours(args):
     return 0
 
 
+# ---- measurement probes behind the roofline and the design notes (--probe) -----------------
+
+def probe_pipes(aes) -> dict:
+    """Integer-pipe issue rates in lanes per SM-clock (the roofline's unit rates), from the
+    library's clock64 microbenchmark (aes_testing_pipe_rate)."""
+    import ctypes
+
+    lib = aes.lib()
+    lib.aes_testing_pipe_rate.restype = ctypes.c_int
+    lib.aes_testing_pipe_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+    names = ["lop3", "iadd", "shf", "prmt", "imad", "shfl (+ add)", "prmt-addressed lds.32 lookup (+ xor)",
+             "imad | lop3 50/50", "shf | lop3 50/50", "prmt | lop3 50/50"]
+    out = {}
+    for op, name in enumerate(names):
+        lanes, mhz = ctypes.c_double(), ctypes.c_double()
+        if lib.aes_testing_pipe_rate(op, 4096, ctypes.byref(lanes), ctypes.byref(mhz)) != 0:
+            raise RuntimeError(f"pipe probe {name} failed")
+        out[name] = {"lanes_per_sm_clock": round(lanes.value, 2), "implied_sm_mhz": round(mhz.value)}
+    return out
+
+
+def probe_corun(aes, torch) -> dict:
+    """The T-table and bitsliced kernels run concurrently on disjoint parts of a 1 GiB buffer
+    (two streams, both after the same event), for bitsliced shares 0 .. 0.2: the premise of
+    the combined roofline (bitsliced warps using the ALU slots the T-table kernel leaves)."""
+    n = NBLOCKS
+    x = torch.randint(0, 256, (n * 16,), dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    ks = aes.aes_key_expand(bytes(range(16)))
+    main_s, sa, sb = torch.cuda.current_stream(), torch.cuda.Stream(), torch.cuda.Stream()
+
+    def launch(nt, nbs):
+        sa.wait_stream(main_s)
+        sb.wait_stream(main_s)
+        aes.aes_crypt_blocks(ks, None, x.data_ptr(), y.data_ptr(), nt, "encrypt", "ttable", sa)
+        if nbs:
+            aes.aes_crypt_blocks(ks, None, x.data_ptr() + nt * 16, y.data_ptr() + nt * 16, nbs, "encrypt", "bitslice", sb)
+        main_s.wait_stream(sa)
+        main_s.wait_stream(sb)
+
+    rows = []
+    for share in (0.0, 0.05, 0.08, 0.10, 0.12, 0.15, 0.20):
+        nbs = (int(n * share) // 1024) * 1024
+        for _ in range(2):
+            launch(n - nbs, nbs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main_s)
+        for _ in range(20):
+            launch(n - nbs, nbs)
+        e1.record(main_s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        rows.append({"bitsliced_share": share, "ms_per_GiB": round(ms, 3), "gbps": round(n * 16 / ms / 1e6, 1)})
+    z = torch.empty_like(x)
+    aes.aes_crypt_blocks(ks, None, x.data_ptr(), z.data_ptr(), n, "encrypt", "ttable")
+    launch(n - (n // 10 // 1024) * 1024, (n // 10 // 1024) * 1024)
+    torch.cuda.synchronize()
+    return {"rows": rows, "split_output_equals_ttable": bool(torch.equal(z, y))}
+
+
+def probe_host_link(aes, torch) -> dict:
+    """Host link rates for 1 GiB: pinned H2D, D2H and both at once with 1, 2, 4 and 8 streams
+    (torch copies), and the library's host-buffer entry point (aes_crypt_host) on pinned
+    buffers, which reads and writes them from the kernel where the device allows it."""
+    import time as _t
+
+    n_bytes = 1 << 30
+    hp = torch.empty(n_bytes, dtype=torch.uint8).pin_memory()
+    hq = torch.empty(n_bytes, dtype=torch.uint8).pin_memory()
+    dg = torch.empty(n_bytes, dtype=torch.uint8, device="cuda")
+    dh = torch.empty(n_bytes, dtype=torch.uint8, device="cuda")
+
+    def rate(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        t = _t.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return round(n_bytes * reps / (_t.perf_counter() - t) / 1e9, 1)
+
+    out = {}
+    for k in (1, 2, 4, 8):
+        streams = [torch.cuda.Stream() for _ in range(k)]
+        chunk = n_bytes // k
+
+        def h2d():
+            for i, st in enumerate(streams):
+                with torch.cuda.stream(st):
+                    dg[i * chunk:(i + 1) * chunk].copy_(hp[i * chunk:(i + 1) * chunk], non_blocking=True)
+
+        def d2h():
+            for i, st in enumerate(streams):
+                with torch.cuda.stream(st):
+                    hq[i * chunk:(i + 1) * chunk].copy_(dh[i * chunk:(i + 1) * chunk], non_blocking=True)
+
+        out[f"h2d_gbs_streams{k}"] = rate(h2d)
+        out[f"d2h_gbs_streams{k}"] = rate(d2h)
+        out[f"both_ways_gbs_each_streams{k}"] = rate(lambda: (h2d(), d2h()))
+    ks = aes.aes_key_expand(bytes(16))
+    out["aes_crypt_host_pinned_gbs"] = rate(
+        lambda: aes.aes_crypt_host(ks, None, hp.data_ptr(), hq.data_ptr(), n_bytes // 16, "encrypt"), reps=3)
+    return out
+
+
+def run_probe(which: str) -> int:
+    import torch
+
+    import paper_1506_08503_gb300 as aes
+
+    torch.cuda.set_device(0)
+    fn = {"pipes": lambda: probe_pipes(aes), "corun": lambda: probe_corun(aes, torch),
+          "host-link": lambda: probe_host_link(aes, torch)}[which]
+    print(json.dumps({"probe": which, "device": torch.cuda.get_device_name(0), "result": fn()}))
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.probe:
+        return run_probe(args.probe)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
