@@ -1,6 +1,7 @@
-/* aesgb_testing.h -- test hooks into host-side logic of libaesgb.so.  They touch no GPU, so the
- * CPU test suite can check the logic directly.  Not part of the stable interface: signatures
- * may change with the implementation they expose. */
+/* aesgb_testing.h -- test hooks into host-side logic of libaesgb.so, which touch no GPU (so the
+ * CPU test suite can check the logic directly), and one measurement hook that runs on the
+ * GPU (aes_testing_pipe_rate, the roofline's unit rates).  Not part of the stable interface:
+ * signatures may change with the implementation they expose. */
 #ifndef AESGB_TESTING_H
 #define AESGB_TESTING_H
 
