@@ -282,13 +282,17 @@ aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsg
  * Same cipher and message rules as aes_batch_run, except that the caller passes the expanded
  * schedules directly (host array of nkeys <= 256 entries; msgs[i].key_idx indexes it) and at
  * most 4096 messages; larger counts are AES_EINVAL.  Nothing is allocated: all working data
- * lives in one static 320 KiB array in device memory that the library declares (present on
- * every device that loads the library, until the process exits).  The first call on a device
- * looks up that array's device address; make that first call before any stream capture.  The
- * call copies its descriptors from pageable host memory, so it returns only after the work
- * already queued on cuda_stream has finished.  All calls share the array: calls on one stream
- * are ordered and safe, calls that overlap on the GPU (other streams, no synchronisation)
- * race on it and may produce wrong output. */
+ * (keys, descriptors, block starts, per-warp slices) lives in one static 416 KiB array in
+ * device memory that the library declares, present on every device that loads the library
+ * until the process exits.  The first call on a device may load the library's device code
+ * (with lazy module loading that is where the array itself comes into being) and looks up
+ * the array's device address; make that first call before any stream capture.  A call on a
+ * stream that is being captured returns AES_EINVAL: the descriptors are staged in one shared
+ * host buffer, so a captured copy would replay whatever that buffer held last.  The call may
+ * block the host while it stages its descriptors from pageable memory; the device array is
+ * updated in stream order.  All calls share the array: calls on one stream are ordered and
+ * safe, calls that overlap on the GPU (other streams, no synchronisation) race on it and may
+ * produce wrong output. */
 aes_status aes_crypt_batched_noalloc(const aes_key_schedule* schedules, uint32_t nkeys, const aes_msg* msgs,
                                      size_t nmsgs, const void* d_in, void* d_out, size_t buf_bytes,
                                      void* cuda_stream);
@@ -337,7 +341,7 @@ typedef struct {
   double gbps;                            /* bytes_completed / (last completion - first submit) */
   double mean_batch;                      /* requests per launch */
   double gbps_from_first_launch;          /* bytes_completed / (last completion - first launch) */
-} aes_server_stats;
+} aes_stats;
 
 /* Starts a server on the current device over `pool` (which must outlive the server).  The
  * staging arena of cfg->hbm_budget bytes is allocated now; AES_ENOMEM if it does not fit. */
@@ -359,7 +363,11 @@ aes_status aes_server_submit_many(aes_server* s, const aes_request* reqs, size_t
  * AES_ETIMEDOUT with *state = AES_REQ_PENDING, or AES_ENOTFOUND for an unknown ticket. */
 aes_status aes_server_poll(aes_server* s, uint64_t ticket, int64_t timeout_us, int* state);
 
-aes_status aes_server_stats_get(aes_server* s, aes_server_stats* out);
+/* Counters and latency percentiles since the last reset, written to *out (host). */
+aes_status aes_server_stats(aes_server* s, aes_stats* out);
+/* The same call under its earlier name. */
+aes_status aes_server_stats_get(aes_server* s, aes_stats* out);
+/* Clears the counters and the latency record. */
 aes_status aes_server_stats_reset(aes_server* s);
 
 /* Fails every queued request, waits for the batches on the GPU, joins the thread and frees

@@ -75,7 +75,7 @@ class aes_request(ctypes.Structure):
                 ("dst_on_device", ctypes.c_uint32)]
 
 
-class aes_server_stats(ctypes.Structure):
+class aes_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "queued", "inflight", "launches",
                                                 "bytes_completed")] + \
                [(n, ctypes.c_double) for n in ("p50_us", "p99_us", "max_us", "mean_us", "gbps", "mean_batch",
@@ -133,7 +133,8 @@ _SIGS: dict[str, tuple] = {
     "aes_server_submit": (_I, [_VP, ctypes.POINTER(aes_request), ctypes.POINTER(ctypes.c_uint64)]),
     "aes_server_submit_many": (_I, [_VP, _VP, _SZ, _VP]),
     "aes_server_poll": (_I, [_VP, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(_I)]),
-    "aes_server_stats_get": (_I, [_VP, ctypes.POINTER(aes_server_stats)]),
+    "aes_server_stats": (_I, [_VP, ctypes.POINTER(aes_stats)]),
+    "aes_server_stats_get": (_I, [_VP, ctypes.POINTER(aes_stats)]),
     "aes_server_stats_reset": (_I, [_VP]),
     "aes_server_destroy": (_I, [_VP]),
 }
@@ -518,8 +519,8 @@ class Server:
         return st.value
 
     def stats(self) -> dict:
-        out = aes_server_stats()
-        _check(lib().aes_server_stats_get(self.handle, ctypes.byref(out)))
+        out = aes_stats()
+        _check(lib().aes_server_stats(self.handle, ctypes.byref(out)))
         return out.as_dict()
 
     def reset_stats(self) -> None:

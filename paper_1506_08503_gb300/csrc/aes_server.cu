@@ -669,7 +669,7 @@ aes_status aes_server_poll(aes_server* s, uint64_t ticket, int64_t timeout_us, i
   return AES_OK;
 }
 
-aes_status aes_server_stats_get(aes_server* s, aes_server_stats* out) {
+aes_status aes_server_stats(aes_server* s, aes_stats* out) {
   clear_error();
   if (!s || !out) return set_error(AES_EINVAL, "null server or output");
   std::vector<double> lat;
@@ -704,6 +704,8 @@ aes_status aes_server_stats_get(aes_server* s, aes_server_stats* out) {
   }
   return AES_OK;
 }
+
+aes_status aes_server_stats_get(aes_server* s, aes_stats* out) { return aes_server_stats(s, out); }
 
 aes_status aes_server_stats_reset(aes_server* s) {
   clear_error();

@@ -25,6 +25,10 @@ def test_header_declares_core_entry_points():
     names = declared_functions()
     for n in ("aes_key_expand", "aes_encrypt_blocks", "aes_decrypt_blocks", "aes_crypt_blocks", "aes_last_error"):
         assert n in names
+    # the boundary's key-pool, batched and server calls under their contract names
+    for n in ("aes_keypool_create", "aes_keypool_set", "aes_keypool_destroy", "aes_crypt_batched",
+              "aes_server_create", "aes_server_submit", "aes_server_poll", "aes_server_stats", "aes_server_destroy"):
+        assert n in names, n
 
 
 def test_library_exports_every_declared_symbol(aes):
