@@ -65,13 +65,42 @@ def roofline_peak_gbs(sms: int, mhz: float) -> float:
     return blocks_per_sm_clock() * sms * mhz * 1e6 * 16 / 1e9
 
 
+def lds_path_bound_gbs(sms: int, mhz: float, wavefronts_per_block: float) -> float:
+    """A table-lookup kernel's own ceiling: one 128-byte shared-memory wavefront per SM-clock,
+    `wavefronts_per_block` of them per 16-byte block (lookups plus the block's load and store,
+    1/8 wavefront each)."""
+    return sms * mhz * 1e6 / wavefronts_per_block * 16 / 1e9
+
+
+def ttable_wavefronts(nr: int) -> float:
+    """16 conflict-free lookups (half a wavefront) per round, plus the block's load and store."""
+    return nr / 2.0 + 0.25
+
+
+# GCM adds 2.5 wavefronts of GHASH lookups per block to the counter-mode data pass
+GCM_WAVEFRONTS = ttable_wavefronts(10) + 2.5
+
+
+def hbm_peak_gbs() -> float:
+    """Measured copy bandwidth (read + write bytes per second) of the GB300s."""
+    f = ROOT / "MEASURED_PEAKS.json"
+    try:
+        return float(json.loads(f.read_text())["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6774.2  # the same measurement as recorded when the file is absent
+
+
+def logic_bound_gbs(sms: int, mhz: float, lane_ops_per_block: float = BS_ALU) -> float:
+    """The gate-level bound: the ALU pipe's 64 lanes per SM-clock over the lane-operations a
+    bitsliced block needs (356.25 for AES-128 at two gates per LOP3)."""
+    return sms * mhz * 1e6 * ALU_LANES / lane_ops_per_block * 16 / 1e9
+
+
 # ---------------------------------------------------------------------------------------------
 
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--probe", choices=["pipes", "corun", "host-link"], default=None,
-                   help="run one measurement probe behind the roofline or a design note, print its JSON, exit")
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -224,6 +253,84 @@ def read_profile() -> dict:
         elif key in ("ncu_encrypt", "ncu_decrypt"):
             out["ncu"][key[4:]] = {k: float(v) for k, v in (kv.split("=") for kv in rest.split())}
     return out
+
+
+def measure_bitsliced(aes, torch, dev, x, n: int, key: bytes, sms: int) -> dict:
+    """The constant-time bitsliced kernel on the benchmark's 1 GiB buffer (AES-128, 10 launches
+    per direction after 2 warm-ups, CUDA events), against its gate-level bound."""
+    stream = torch.cuda.current_stream()
+    ks = aes.aes_key_expand(key)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    out = {}
+    for d, src, dst in (("encrypt", x, y), ("decrypt", y, z)):
+        for _ in range(2):
+            aes.aes_crypt_blocks(ks, None, src.data_ptr(), dst.data_ptr(), n, d, "bitslice")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            aes.aes_crypt_blocks(ks, None, src.data_ptr(), dst.data_ptr(), n, d, "bitslice")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[d + "_gbs"] = n * 16 / (e0.elapsed_time(e1) / 10 / 1e3) / 1e9
+    if not torch.equal(z, x):
+        raise RuntimeError("bitsliced round trip failed")
+    bound = logic_bound_gbs(sms, SM_MAX_MHZ_NOMINAL)
+    out.update({"logic_bound_gbs": bound, "encrypt_frac": out["encrypt_gbs"] / bound,
+                "decrypt_frac": out["decrypt_gbs"] / bound,
+                "bound_source": f"{sms} SMs x {SM_MAX_MHZ_NOMINAL:.0f} MHz x {ALU_LANES:.0f} lanes / "
+                                f"{BS_ALU} lane-ops per block x 16 B"})
+    del y, z
+    return out
+
+
+def summary_of(line: dict, sms: int) -> dict:
+    """The headline figures of every configuration in one small object, printed last on the line."""
+    mhz = SM_MAX_MHZ_NOMINAL
+    r = line["roofline"]
+    s = {"plain_1GiB": {"gbs": line["value"], "enc_gbs": r["enc_gbs"], "dec_gbs": r["dec_gbs"], "frac": r["frac"],
+                        "frac_of_lds_path_bound": r["frac_of_lds_path_bound"]},
+         "e2e_gbs": (line.get("e2e") or {}).get("value")}
+    bs = line.get("bitsliced")
+    if bs:
+        s["bitsliced_1GiB"] = {k: bs[k] for k in ("encrypt_gbs", "decrypt_gbs", "encrypt_frac", "decrypt_frac",
+                                                 "logic_bound_gbs")}
+    b = line.get("batched")
+    if b:
+        s["batched_4096_msgs"] = {"gbs": b["value"], "vs_plain_kernel": b["vs_plain_kernel"],
+                                  "vs_plain_kernel_same_bytes": b["vs_plain_kernel_same_bytes"]}
+        if b.get("with_ivs"):
+            s["batched_4096_msgs"]["with_ivs_gbs"] = b["with_ivs"]["value"]
+    f = line.get("followons")
+    if f:
+        b10, b14 = (lds_path_bound_gbs(sms, mhz, ttable_wavefronts(nr)) for nr in (10, 14))
+        sen = f["sensor_1e7_records"]
+        s["sensor_1e7_records"] = {
+            "aes128_enc_gbs": sen["aes128_encrypt_gbs"], "aes128_frac": sen["aes128_encrypt_gbs"] / b10,
+            "aes256_enc_gbs": sen["aes256_encrypt_gbs"], "aes256_frac": sen["aes256_encrypt_gbs"] / b14,
+            "bounds_gbs": {"aes128": b10, "aes256": b14}}
+        gb = lds_path_bound_gbs(sms, mhz, GCM_WAVEFRONTS)
+        s["ctr_1GiB"] = {"gbs": f["ctr_1GiB_gbs"], "frac": f["ctr_1GiB_gbs"] / b10, "bound_gbs": b10}
+        s["gcm_1GiB"] = {"enc_gbs": f["gcm_1GiB_encrypt_gbs"], "dec_gbs": f["gcm_1GiB_decrypt_gbs"],
+                         "frac": f["gcm_1GiB_encrypt_gbs"] / gb, "bound_gbs": gb}
+        s["scan_1e7_records"] = {"gbs": f["scan_1e7_records_gbs"], "frac": f["scan_frac_of_measured_copy_bw"]}
+        sm = f.get("small_4096_blocks")
+        if sm:
+            s["small_4096_blocks_us"] = {k: sm[k] for k in ("encrypt_us_median", "encrypt_graph_replay_us_median",
+                                                           "decrypt_us_median", "decrypt_graph_replay_us_median")}
+    c = line.get("cbc")
+    if c:
+        s["cbc"] = [{"msgs": row["messages"], "blocks": row["blocks_per_message"], "enc_gbs": row["encrypt_gbs"],
+                     "dec_gbs": row["decrypt_gbs"]} for row in c["rows"]]
+    v = line.get("served")
+    if v:
+        cl = v["closed_loop"]
+        s["served"] = {"closed_loop": {k: cl[k] for k in ("gbps", "gbps_from_first_launch",
+                                                          "vs_plain_kernel_same_rounds_wall",
+                                                          "vs_plain_kernel_same_rounds", "p50_us", "p99_us")},
+                       "rates": [{"rate": e["offered_rate"], "p50_us": e["p50_us"], "p99_us": e["p99_us"]}
+                                 for e in v["rates"]]}
+    return s
 
 
 def measure_batched(aes, torch, dev, steps: int, plain_gbs: float, fixed_shape=None) -> dict:
@@ -508,8 +615,12 @@ def measure_served(aes, torch, dev, nreq: int, plain_gbs: float) -> dict:
             if rate:
                 states = [srv.poll(t) for t in tickets]
                 st = srv.stats()
+            # completed requests over the server's own window (first submit to last completion),
+            # the same window as its gbps
+            window_s = st["bytes_completed"] / (st["gbps"] * 1e9) if st["gbps"] > 0 else float("nan")
             entry = {"offered_rate": rate if rate else "closed-loop", "requests": len(tickets),
-                     "achieved_rate": len(tickets) / max(1e-9, (_t.perf_counter() - t0) if rate else dt),
+                     "achieved_rate": st["completed"] / window_s if st["gbps"] > 0 else None,
+                     "window": "server clock, first submit to last completion (achieved_rate and gbps)",
                      "p50_us": st["p50_us"], "p99_us": st["p99_us"], "max_us": st["max_us"], "gbps": st["gbps"],
                      "gbps_from_first_launch": st["gbps_from_first_launch"],
                      "mean_batch": st["mean_batch"], "launches": st["launches"],
@@ -707,10 +818,10 @@ def run_ours(args):
                 "enc_gbs_median": n * 16 / (statistics.median(enc_ms) / 1e3) / 1e9,
                 "dec_gbs_median": n * 16 / (statistics.median(dec_ms) / 1e3) / 1e9,
                 "enc_gbs_best": n * 16 / (min(enc_ms) / 1e3) / 1e9, "dec_gbs_best": n * 16 / (min(dec_ms) / 1e3) / 1e9,
-                "hbm_term_gbs": 6774.2 / 2,
+                "hbm_term_gbs": hbm_peak_gbs() / 2,
                 # the T-table design's own ceiling: 160 lookups (5 wavefronts) plus the block's
                 # 16-byte load and store (1/8 wavefront each) through the L1/shared-memory path
-                "lds_path_bound_gbs": sms * SM_MAX_MHZ_NOMINAL * 1e6 / 5.25 * 16 / 1e9}
+                "lds_path_bound_gbs": lds_path_bound_gbs(sms, SM_MAX_MHZ_NOMINAL, ttable_wavefronts(10))}
     roofline["frac_of_lds_path_bound"] = achieved / roofline["lds_path_bound_gbs"]
 
     # ---- the same launches in place (output over input), outside the timed region ------------
@@ -736,6 +847,10 @@ def run_ours(args):
                     "decrypt_gbs_median": n * 16 / (statistics.median(ip_dec) / 1e3) / 1e9,
                     "encrypt_gbs_best": n * 16 / (min(ip_enc) / 1e3) / 1e9,
                     "decrypt_gbs_best": n * 16 / (min(ip_dec) / 1e3) / 1e9, "repetitions": 10}
+
+    bitsliced = None
+    if extras and args.kernel != "bitslice":
+        bitsliced = measure_bitsliced(aes, torch, dev, x, n, key, sms)
 
     batched = None
     if not args.no_batched and extras:
@@ -789,136 +904,18 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "nblocks_per_rank": n, "key_bits": 128, "mode": "ECB (IV = 0)",
                        "kernel": args.kernel, "tuned": tuned, "l2": "inputs (1 GiB) larger than L2 (129 MB); no flush"},
             "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk, "roofline": roofline,
-            "cpu_baseline": cpu, "batched": batched, "served": served, "cbc": cbc, "followons": followons, "in_place": in_place,
+            "cpu_baseline": cpu, "bitsliced": bitsliced, "batched": batched, "served": served, "cbc": cbc,
+            "followons": followons, "in_place": in_place,
         }
+        line["summary"] = summary_of(line, sms)  # last, so that a kept tail of the line holds it
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
     return 0
 
 
-# ---- measurement probes behind the roofline and the design notes (--probe) -----------------
-
-def probe_pipes(aes) -> dict:
-    """Integer-pipe issue rates in lanes per SM-clock (the roofline's unit rates), from the
-    library's clock64 microbenchmark (aes_testing_pipe_rate)."""
-    import ctypes
-
-    lib = aes.lib()
-    lib.aes_testing_pipe_rate.restype = ctypes.c_int
-    lib.aes_testing_pipe_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                                          ctypes.POINTER(ctypes.c_double)]
-    names = ["lop3", "iadd", "shf", "prmt", "imad", "shfl (+ add)", "prmt-addressed lds.32 lookup (+ xor)",
-             "imad | lop3 50/50", "shf | lop3 50/50", "prmt | lop3 50/50"]
-    out = {}
-    for op, name in enumerate(names):
-        lanes, mhz = ctypes.c_double(), ctypes.c_double()
-        if lib.aes_testing_pipe_rate(op, 4096, ctypes.byref(lanes), ctypes.byref(mhz)) != 0:
-            raise RuntimeError(f"pipe probe {name} failed")
-        out[name] = {"lanes_per_sm_clock": round(lanes.value, 2), "implied_sm_mhz": round(mhz.value)}
-    return out
-
-
-def probe_corun(aes, torch) -> dict:
-    """The T-table and bitsliced kernels run concurrently on disjoint parts of a 1 GiB buffer
-    (two streams, both after the same event), for bitsliced shares 0 .. 0.2: the premise of
-    the combined roofline (bitsliced warps using the ALU slots the T-table kernel leaves)."""
-    n = NBLOCKS
-    x = torch.randint(0, 256, (n * 16,), dtype=torch.uint8, device="cuda")
-    y = torch.empty_like(x)
-    ks = aes.aes_key_expand(bytes(range(16)))
-    main_s, sa, sb = torch.cuda.current_stream(), torch.cuda.Stream(), torch.cuda.Stream()
-
-    def launch(nt, nbs):
-        sa.wait_stream(main_s)
-        sb.wait_stream(main_s)
-        aes.aes_crypt_blocks(ks, None, x.data_ptr(), y.data_ptr(), nt, "encrypt", "ttable", sa)
-        if nbs:
-            aes.aes_crypt_blocks(ks, None, x.data_ptr() + nt * 16, y.data_ptr() + nt * 16, nbs, "encrypt", "bitslice", sb)
-        main_s.wait_stream(sa)
-        main_s.wait_stream(sb)
-
-    rows = []
-    for share in (0.0, 0.05, 0.08, 0.10, 0.12, 0.15, 0.20):
-        nbs = (int(n * share) // 1024) * 1024
-        for _ in range(2):
-            launch(n - nbs, nbs)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(main_s)
-        for _ in range(20):
-            launch(n - nbs, nbs)
-        e1.record(main_s)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / 20
-        rows.append({"bitsliced_share": share, "ms_per_GiB": round(ms, 3), "gbps": round(n * 16 / ms / 1e6, 1)})
-    z = torch.empty_like(x)
-    aes.aes_crypt_blocks(ks, None, x.data_ptr(), z.data_ptr(), n, "encrypt", "ttable")
-    launch(n - (n // 10 // 1024) * 1024, (n // 10 // 1024) * 1024)
-    torch.cuda.synchronize()
-    return {"rows": rows, "split_output_equals_ttable": bool(torch.equal(z, y))}
-
-
-def probe_host_link(aes, torch) -> dict:
-    """Host link rates for 1 GiB: pinned H2D, D2H and both at once with 1, 2, 4 and 8 streams
-    (torch copies), and the library's host-buffer entry point (aes_crypt_host) on pinned
-    buffers, which reads and writes them from the kernel where the device allows it."""
-    import time as _t
-
-    n_bytes = 1 << 30
-    hp = torch.empty(n_bytes, dtype=torch.uint8).pin_memory()
-    hq = torch.empty(n_bytes, dtype=torch.uint8).pin_memory()
-    dg = torch.empty(n_bytes, dtype=torch.uint8, device="cuda")
-    dh = torch.empty(n_bytes, dtype=torch.uint8, device="cuda")
-
-    def rate(fn, reps=5):
-        fn()
-        torch.cuda.synchronize()
-        t = _t.perf_counter()
-        for _ in range(reps):
-            fn()
-        torch.cuda.synchronize()
-        return round(n_bytes * reps / (_t.perf_counter() - t) / 1e9, 1)
-
-    out = {}
-    for k in (1, 2, 4, 8):
-        streams = [torch.cuda.Stream() for _ in range(k)]
-        chunk = n_bytes // k
-
-        def h2d():
-            for i, st in enumerate(streams):
-                with torch.cuda.stream(st):
-                    dg[i * chunk:(i + 1) * chunk].copy_(hp[i * chunk:(i + 1) * chunk], non_blocking=True)
-
-        def d2h():
-            for i, st in enumerate(streams):
-                with torch.cuda.stream(st):
-                    hq[i * chunk:(i + 1) * chunk].copy_(dh[i * chunk:(i + 1) * chunk], non_blocking=True)
-
-        out[f"h2d_gbs_streams{k}"] = rate(h2d)
-        out[f"d2h_gbs_streams{k}"] = rate(d2h)
-        out[f"both_ways_gbs_each_streams{k}"] = rate(lambda: (h2d(), d2h()))
-    ks = aes.aes_key_expand(bytes(16))
-    out["aes_crypt_host_pinned_gbs"] = rate(
-        lambda: aes.aes_crypt_host(ks, None, hp.data_ptr(), hq.data_ptr(), n_bytes // 16, "encrypt"), reps=3)
-    return out
-
-
-def run_probe(which: str) -> int:
-    import torch
-
-    import paper_1506_08503_gb300 as aes
-
-    torch.cuda.set_device(0)
-    fn = {"pipes": lambda: probe_pipes(aes), "corun": lambda: probe_corun(aes, torch),
-          "host-link": lambda: probe_host_link(aes, torch)}[which]
-    print(json.dumps({"probe": which, "device": torch.cuda.get_device_name(0), "result": fn()}))
-    return 0
-
-
 def main():
     args = parse_args()
-    if args.probe:
-        return run_probe(args.probe)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

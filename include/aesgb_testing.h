@@ -1,7 +1,6 @@
-/* aesgb_testing.h -- test hooks into host-side logic of libaesgb.so, which touch no GPU (so the
- * CPU test suite can check the logic directly), and one measurement hook that runs on the
- * GPU (aes_testing_pipe_rate, the roofline's unit rates).  Not part of the stable interface:
- * signatures may change with the implementation they expose. */
+/* aesgb_testing.h -- test hooks into host-side logic of libaesgb.so.  They touch no GPU, so the
+ * CPU test suite can check the logic directly.  Not part of the stable interface: signatures
+ * may change with the implementation they expose. */
 #ifndef AESGB_TESTING_H
 #define AESGB_TESTING_H
 
@@ -32,15 +31,6 @@ int aes_testing_arena(size_t size, const int64_t* ops, size_t nops, int64_t* res
  * (a compiled candidate), 0 otherwise; store returns 0. */
 int aes_testing_tune_cache_store(const char* path, const char* sig, int impl, int threads, int unroll, double us);
 int aes_testing_tune_cache_lookup(const char* path, const char* sig, int* impl, int* threads, int* unroll);
-
-/* Measures on the current device the issue rate of one integer instruction kind, in lanes per
- * SM-clock (the unit rates of the on-chip roofline): op 0 LOP3, 1 IADD, 2 SHF, 3 PRMT, 4 IMAD,
- * 5 SHFL (counted with the add that consumes it), 6 a PRMT-addressed 4-byte shared-memory
- * lookup XORed in (counting lookups), 7 / 8 / 9 IMAD / SHF / PRMT alternating with LOP3.  One
- * 1024-thread CTA per SM runs `iters` (1..65536) trips of 128 operations per thread, timed with
- * clock64; *implied_mhz is the SM clock those cycles imply over the CUDA-event time.  Runs
- * synchronously (about iters x 1 us).  Returns 0, or -1 for a bad argument or a CUDA error. */
-int aes_testing_pipe_rate(int op, int iters, double* lanes_per_clk, double* implied_mhz);
 
 #ifdef __cplusplus
 }

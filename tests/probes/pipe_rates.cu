@@ -1,23 +1,22 @@
-// aes_probe.cu -- the integer-pipe rates the on-chip roofline is built from, measured on the
-// device: lanes per SM-clock for three-input logic (LOP3), adds, funnel shifts, byte permutes,
-// integer multiply-adds, warp shuffles, byte-permute-addressed shared-memory lookups, and
-// half-and-half mixes (to see whether two kinds issue beside each other).
+// pipe_rates.cu -- measures on one GPU the issue rates (lanes per SM-clock) of the integer
+// instructions the on-chip AES roofline is built from: three-input logic (LOP3), adds, funnel
+// shifts, byte permutes, integer multiply-adds, warp shuffles, byte-permute-addressed
+// shared-memory lookups, and half-and-half mixes (to see whether two kinds issue side by side).
+// A standalone measurement program for the test suite (tests/test_gpu_probes.py), not part of
+// the library.
 //
 // One CTA of 1024 threads per SM (its dynamic shared memory leaves room for no second CTA),
 // eight independent dependency chains per thread, 16 x 8 operations per loop trip; the cycle
 // count of each CTA comes from clock64 between two barriers, so the rate does not depend on
 // the clock frequency.  The operations are inline PTX, so the compiler cannot fold them.
+// Prints one JSON object: {"<mix>": {"lanes_per_sm_clock": x, "implied_sm_mhz": f}, ...}.
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
 #include <vector>
 
-#include "aes_internal.cuh"
-#include "aesgb_testing.h"
-
-namespace aesgb {
 namespace {
-
 __device__ __forceinline__ uint32_t p_lop3_96(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
   asm volatile("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
@@ -116,13 +115,11 @@ ProbeFn probe_kernel(int op) {
 }
 
 }  // namespace
-}  // namespace aesgb
 
-using namespace aesgb;
-
-extern "C" int aes_testing_pipe_rate(int op, int iters, double* lanes_per_clk, double* implied_mhz) {
+// Rate of one mix: 0 on success.
+static int pipe_rate(int op, int iters, double* lanes_per_clk, double* implied_mhz) {
   ProbeFn k = probe_kernel(op);
-  if (!k || iters < 1 || iters > (1 << 16) || !lanes_per_clk || !implied_mhz) return -1;
+  if (!k || iters < 1 || iters > (1 << 16)) return -1;
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || nsm <= 0) return -1;
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem) !=
@@ -164,4 +161,24 @@ extern "C" int aes_testing_pipe_rate(int op, int iters, double* lanes_per_clk, d
   cudaFree(d_out);
   cudaFree(d_cyc);
   return rc;
+}
+
+int main() {
+  static const char* names[] = {"lop3", "iadd", "shf", "prmt", "imad", "shfl (+ add)",
+                                "prmt-addressed lds.32 lookup (+ xor)", "imad | lop3 50/50", "shf | lop3 50/50",
+                                "prmt | lop3 50/50"};
+  int sms = 0, mhz = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  cudaDeviceGetAttribute(&mhz, cudaDevAttrClockRate, 0);
+  std::printf("{\"sms\": %d, \"clock_khz\": %d", sms, mhz);
+  for (int op = 0; op < 10; ++op) {
+    double lanes = 0, implied = 0;
+    if (pipe_rate(op, 4096, &lanes, &implied) != 0) {
+      std::fprintf(stderr, "pipe probe %s failed\n", names[op]);
+      return 1;
+    }
+    std::printf(", \"%s\": {\"lanes_per_sm_clock\": %.2f, \"implied_sm_mhz\": %.0f}", names[op], lanes, implied);
+  }
+  std::printf("}\n");
+  return 0;
 }
