@@ -68,6 +68,10 @@ Layout layout(size_t nenc, size_t ndec, size_t wmax) {
   return l;
 }
 
+}  // namespace
+
+namespace aesgb {
+
 // Work of a direction in round-blocks (a block of an Nr-round key costs Nr).
 uint64_t work_of(const BatchMsg* m, size_t n, const int8_t* rounds) {
   uint64_t w = 0;
@@ -104,7 +108,7 @@ void weighted_slices(const BatchMsg* m, const uint64_t* start, size_t n, const i
   gb[nw] = start[n];
 }
 
-}  // namespace
+}  // namespace aesgb
 
 struct aes_batch {
   aes_keypool* pool = nullptr;

@@ -139,6 +139,13 @@ TTDualFn ttable_batched_dual_r10(int threads, int blocks_per_lane, int nre, int 
 struct aes_batch;
 
 namespace aesgb {
+// Work of a direction in round-blocks: sum of nblocks x rounds[key_idx] over its messages.
+uint64_t work_of(const BatchMsg* m, size_t n, const int8_t* rounds);
+// Cuts a direction's block space (n messages, start[0..n]) into nw slices of equal work W in
+// round-blocks: gb[w] is warp w's first block (gb[nw] = start[n]) and msg[w] the message
+// holding it.
+void weighted_slices(const BatchMsg* m, const uint64_t* start, size_t n, const int8_t* rounds, uint64_t W,
+                     uint64_t nw, uint64_t* gb, uint32_t* msg);
 // Launches one batch from descriptors written by `fill(enc, dec)` (nenc and ndec entries,
 // nblocks > 0 each) relative to in_base / out_base.  The caller holds the batch's lock.
 aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,

@@ -10,10 +10,13 @@
 //
 // The static array is shared by every call on a device and keeps the last call's contents.
 // Nothing in it has to start at zero: each call rewrites every entry its kernels read (keys
-// 0..nkeys-1, its own descriptors and block starts).  Calls issued on the SAME stream are
-// safe: the descriptor upload copies from pageable host memory, which waits for earlier work
-// on that stream.  Calls that overlap on the GPU (different streams, no synchronisation
-// between them) race on the array and may compute with each other's descriptors.
+// 0..nkeys-1, its own descriptors, block starts and per-warp slices).  Calls issued on the
+// SAME stream are safe: the descriptor upload is ordered behind earlier work on that stream.
+// Calls that overlap on the GPU (different streams, no synchronisation between them) race on
+// the array and may compute with each other's descriptors.  The descriptors are built in one
+// shared host buffer, so a call on a stream that is being captured is refused: a graph would
+// replay whatever that buffer held last.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -26,14 +29,18 @@ using namespace aesgb;
 constexpr uint32_t kNoAllocMaxKeys = 256;
 constexpr uint32_t kNoAllocMaxMsgs = 4096;
 constexpr int kThreads = 512, kBlocksPerLane = 2;
+constexpr uint32_t kMaxCtas = 256;                         // per direction (one per SM, at most 256)
+constexpr uint32_t kMaxWarps = kMaxCtas * (kThreads / 32);  // 4096
 
 struct NoAllocScratch {
   PoolEntry keys[kNoAllocMaxKeys];         // 128 KiB
   BatchMsg msgs[kNoAllocMaxMsgs];          // 128 KiB: encryptions first, then decryptions
   uint64_t start[2][kNoAllocMaxMsgs + 1];  // 64 KiB: block starts per direction
+  uint64_t warp_gb[2][kMaxWarps + 1];      // 64 KiB: each warp's first block, slices of equal rounds x blocks
+  uint32_t warp_msg[2][kMaxWarps];         // 32 KiB: the message holding that block
 };
 
-// Device-side scratch: 320 KiB on every GPU that loads the library, held until exit.  In host
+// Device-side scratch: 416 KiB on every GPU that loads the library, held until exit.  In host
 // code this name is only a stand-in; its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
@@ -100,6 +107,13 @@ extern "C" aes_status aes_crypt_batched_noalloc(const aes_key_schedule* schedule
     (m.dir == AES_ENCRYPT ? nenc : ndec)++;
   }
   if (nenc + ndec == 0) return AES_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamIsCapturing");
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(AES_EINVAL, "the stream is being captured: this call stages its descriptors in one shared host "
+                                 "buffer, so it cannot be recorded into a graph");
 
   std::lock_guard<std::mutex> lk(g_mu);
   NoAllocScratch* dev = nullptr;
@@ -109,7 +123,11 @@ extern "C" aes_status aes_crypt_batched_noalloc(const aes_key_schedule* schedule
   if (!di) return AES_ECUDA;
 
   NoAllocScratch& h = g_host_stage;
-  for (uint32_t k = 0; k < nkeys; ++k) fill_entry(schedules[k], h.keys[k]);
+  int8_t rounds[kNoAllocMaxKeys];
+  for (uint32_t k = 0; k < nkeys; ++k) {
+    fill_entry(schedules[k], h.keys[k]);
+    rounds[k] = int8_t(schedules[k].nr);
+  }
   size_t ie = 0, id = nenc;
   uint64_t te = 0, td = 0;
   for (size_t i = 0; i < nmsgs; ++i) {
@@ -122,22 +140,45 @@ extern "C" aes_status aes_crypt_batched_noalloc(const aes_key_schedule* schedule
   h.start[0][nenc] = te;
   h.start[1][ndec] = td;
 
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  cudaError_t e;
-  // Pageable sources: each copy waits for earlier work on `s`, and the staging above may be
-  // reused as soon as the copy call returns.
+  // Grid per direction: one CTA per SM (at most kMaxCtas), fewer when there is less than one
+  // block per thread; every warp gets a slice of equal work in blocks x rounds, so warps
+  // holding 14-round messages do not set the kernel's finish time.
+  uint32_t grid[2] = {0, 0};
+  for (int dir = 0; dir < 2; ++dir) {
+    const uint64_t total = dir == AES_ENCRYPT ? te : td;
+    if (!total) continue;
+    const uint64_t want = (total + kThreads - 1) / kThreads;
+    const uint64_t cap_ctas = std::min<uint64_t>(uint64_t(di->sms), kMaxCtas);
+    grid[dir] = uint32_t(want < cap_ctas ? want : cap_ctas);
+    const BatchMsg* dm = dir == AES_ENCRYPT ? h.msgs : h.msgs + nenc;
+    const size_t n = dir == AES_ENCRYPT ? nenc : ndec;
+    weighted_slices(dm, h.start[dir], n, rounds, work_of(dm, n, rounds), uint64_t(grid[dir]) * (kThreads / 32),
+                    h.warp_gb[dir], h.warp_msg[dir]);
+  }
+
+  // Pageable sources: the copies are ordered behind earlier work on `s`, and the staging
+  // above may be reused as soon as each copy call returns.
   if ((e = cudaMemcpyAsync(dev->keys, h.keys, nkeys * sizeof(PoolEntry), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(dev->msgs, h.msgs, (nenc + ndec) * sizeof(BatchMsg), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(dev->start[0], h.start[0], (nenc + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(dev->start[1], h.start[1], (ndec + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_error(e, "descriptor upload");
+  for (int dir = 0; dir < 2; ++dir) {
+    if (!grid[dir]) continue;
+    const size_t nw = size_t(grid[dir]) * (kThreads / 32);
+    if ((e = cudaMemcpyAsync(dev->warp_gb[dir], h.warp_gb[dir], (nw + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dev->warp_msg[dir], h.warp_msg[dir], nw * sizeof(uint32_t), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+      return cuda_error(e, "slice upload");
+  }
 
   const uint64_t in_base = reinterpret_cast<uint64_t>(d_in), out_base = reinterpret_cast<uint64_t>(d_out);
   for (int dir = 0; dir < 2; ++dir) {
     const uint64_t total = dir == AES_ENCRYPT ? te : td;
     if (!total) continue;
-    const BatchDir bd{dir == AES_ENCRYPT ? dev->msgs : dev->msgs + nenc, dev->start[dir], nullptr, total,
-                      uint32_t(dir == AES_ENCRYPT ? nenc : ndec), 0u};
+    const BatchDir bd{dir == AES_ENCRYPT ? dev->msgs : dev->msgs + nenc, dev->start[dir], dev->warp_msg[dir], total,
+                      uint32_t(dir == AES_ENCRYPT ? nenc : ndec), 0u, dev->warp_gb[dir]};
     const size_t smem = ttable_smem_bytes(dir);
     auto k = dir == AES_ENCRYPT ? tt::tt_batched_kernel<AES_ENCRYPT, kThreads, kBlocksPerLane>
                                 : tt::tt_batched_kernel<AES_DECRYPT, kThreads, kBlocksPerLane>;
@@ -145,9 +186,7 @@ extern "C" aes_status aes_crypt_batched_noalloc(const aes_key_schedule* schedule
       aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(k), smem);
       if (ast != AES_OK) return ast;
     }
-    const uint64_t want = (total + kThreads - 1) / kThreads;
-    const unsigned grid = unsigned(want < uint64_t(di->sms) ? want : uint64_t(di->sms));
-    k<<<grid, kThreads, smem, s>>>(in_base, out_base, bd, dev->keys);
+    k<<<grid[dir], kThreads, smem, s>>>(in_base, out_base, bd, dev->keys);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "batched kernel launch");
   }
   return AES_OK;
