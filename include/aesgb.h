@@ -251,6 +251,16 @@ aes_status aes_batch_create(aes_keypool* pool, size_t max_msgs, aes_batch** out)
 aes_status aes_batch_run(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const void* d_in, void* d_out,
                          size_t buf_bytes, void* cuda_stream);
 
+/* aes_batch_run with one IV per message, the IV matrix V of the paper's Section II (one row
+ * per message): ivs is a host array of nmsgs x 16 bytes (row i belongs to msgs[i]; NULL is
+ * the same as aes_batch_run, zero IVs).  Every block of message i is one of the paper's
+ * one-block CBC messages under that message's key and IV: C = Cipher_K(P xor IV_i) for
+ * encryption, P = InvCipher_K(C) xor IV_i for decryption.  The IV is folded into the round key
+ * that carries it when a warp moves to the message, so it costs nothing per block.  The array
+ * is copied before the call returns.  Other rules as aes_batch_run. */
+aes_status aes_batch_run_iv(aes_batch* b, const aes_msg* msgs, const uint8_t* ivs, size_t nmsgs, const void* d_in,
+                            void* d_out, size_t buf_bytes, void* cuda_stream);
+
 /* Tunes the batch's launch shape on this workload: the CTA size and the blocks each lane
  * enciphers per window; compiled pairs are (512, 1), (512, 2), (512, 4), (384, 4), (256, 4)
  * and, for work that is AES-128 throughout, (768, 1), one CTA per SM.  A direction whose
@@ -273,6 +283,11 @@ aes_status aes_batch_destroy(aes_batch* b);
  * on first use and grown as needed).  Calls on one pool are serialised. */
 aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsgs, const void* d_in,
                              void* d_out, size_t buf_bytes, void* cuda_stream);
+
+/* One-shot form of aes_batch_run_iv (per-message IVs, Section II's V), through the same
+ * internal batch context as aes_crypt_batched. */
+aes_status aes_crypt_batched_iv(aes_keypool* pool, const aes_msg* msgs, const uint8_t* ivs, size_t nmsgs,
+                                const void* d_in, void* d_out, size_t buf_bytes, void* cuda_stream);
 
 /* Batched encryption/decryption for callers that may not allocate device memory: for
  * example a plug-in whose host application owns all device memory and only lends it input

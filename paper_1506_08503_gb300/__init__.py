@@ -126,9 +126,11 @@ _SIGS: dict[str, tuple] = {
     "aes_batch_run": (_I, [_VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "aes_batch_autotune": (_I, [_VP, _VP, _SZ, _VP, _VP, _SZ, ctypes.c_char_p, ctypes.POINTER(_I),
                                 ctypes.POINTER(_I), _VP]),
+    "aes_batch_run_iv": (_I, [_VP, _VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "aes_batch_set_shape": (_I, [_VP, _I, _I]),
     "aes_batch_destroy": (_I, [_VP]),
     "aes_crypt_batched": (_I, [_VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
+    "aes_crypt_batched_iv": (_I, [_VP, _VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "aes_server_create": (_I, [ctypes.POINTER(aes_server_cfg), _VP, ctypes.POINTER(_VP)]),
     "aes_server_submit": (_I, [_VP, ctypes.POINTER(aes_request), ctypes.POINTER(ctypes.c_uint64)]),
     "aes_server_submit_many": (_I, [_VP, _VP, _SZ, _VP]),
@@ -440,9 +442,15 @@ class Batch:
         _check(lib().aes_batch_create(pool.handle, max_msgs, ctypes.byref(h)))
         self.handle, self.pool = h, pool
 
-    def run(self, msgs, d_in: int, d_out: int, buf_bytes: int, stream=None) -> None:
+    def run(self, msgs, d_in: int, d_out: int, buf_bytes: int, stream=None, ivs=None) -> None:
+        """ivs: None, or a host uint8 array of len(msgs) x 16 bytes (one IV per message)."""
         a, p, n = _msgs_ptr(msgs)
-        _check(lib().aes_batch_run(self.handle, p, n, d_in, d_out, buf_bytes, _stream_ptr(stream)))
+        if ivs is None:
+            _check(lib().aes_batch_run(self.handle, p, n, d_in, d_out, buf_bytes, _stream_ptr(stream)))
+        else:
+            v = _ivs_array(ivs, n)
+            _check(lib().aes_batch_run_iv(self.handle, p, v.ctypes.data, n, d_in, d_out, buf_bytes,
+                                          _stream_ptr(stream)))
 
     def autotune(self, msgs, d_in: int, d_out: int, buf_bytes: int, cache_path: str | None = None,
                  stream=None) -> tuple[int, int]:
@@ -471,6 +479,21 @@ class Batch:
 def aes_crypt_batched(pool: KeyPool, msgs, d_in: int, d_out: int, buf_bytes: int, stream=None) -> None:
     a, p, n = _msgs_ptr(msgs)
     _check(lib().aes_crypt_batched(pool.handle, p, n, d_in, d_out, buf_bytes, _stream_ptr(stream)))
+
+
+def _ivs_array(ivs, n: int):
+    import numpy as np
+    v = np.ascontiguousarray(np.asarray(ivs, dtype=np.uint8).reshape(-1))
+    if v.size != 16 * n:
+        raise ValueError("ivs must hold 16 bytes per message")
+    return v
+
+
+def aes_crypt_batched_iv(pool: KeyPool, msgs, ivs, d_in: int, d_out: int, buf_bytes: int, stream=None) -> None:
+    """aes_crypt_batched with one 16-byte IV per message (ivs: host uint8, len(msgs) x 16)."""
+    a, p, n = _msgs_ptr(msgs)
+    v = _ivs_array(ivs, n)
+    _check(lib().aes_crypt_batched_iv(pool.handle, p, v.ctypes.data, n, d_in, d_out, buf_bytes, _stream_ptr(stream)))
 
 
 # ---- server -----------------------------------------------------------------------------------

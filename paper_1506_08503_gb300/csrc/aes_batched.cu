@@ -50,7 +50,7 @@ struct Slot {
 };
 
 struct Layout {
-  size_t enc_msgs, dec_msgs, enc_start, dec_start, enc_gb, dec_gb, enc_warp, dec_warp, end;
+  size_t enc_msgs, dec_msgs, enc_start, dec_start, enc_gb, dec_gb, enc_warp, dec_warp, end, enc_iv, dec_iv, end_iv;
 };
 
 // wmax: most warps a launch can have (SMs x the largest shape's threads / 32)
@@ -65,6 +65,10 @@ Layout layout(size_t nenc, size_t ndec, size_t wmax) {
   l.enc_warp = l.dec_gb + (wmax + 1) * sizeof(uint64_t);
   l.dec_warp = l.enc_warp + wmax * sizeof(uint32_t);
   l.end = l.dec_warp + wmax * sizeof(uint32_t);
+  // per-message IVs (uploaded only by runs that carry them), 16-byte aligned
+  l.enc_iv = (l.end + 15) & ~size_t(15);
+  l.dec_iv = l.enc_iv + nenc * 16;
+  l.end_iv = l.dec_iv + ndec * 16;
   return l;
 }
 
@@ -186,9 +190,8 @@ namespace aesgb {
 
 // Writes nenc + ndec descriptors through `fill` into the next staging slot, computes the
 // per-direction block starts and launches the graph on `stream`.  Caller holds b->mu.
-aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
-                              const std::function<void(BatchMsg*, BatchMsg*)>& fill, uint64_t in_base,
-                              uint64_t out_base, cudaStream_t stream) {
+aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec, const DescFill& fill, bool with_ivs,
+                              uint64_t in_base, uint64_t out_base, cudaStream_t stream) {
   cudaError_t e;
   if (nenc + ndec > b->max_msgs) return set_error(AES_EINVAL, "%zu messages exceed the batch capacity %zu", nenc + ndec, b->max_msgs);
   Slot& s = b->slot[b->next];
@@ -200,7 +203,9 @@ aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
   BatchMsg* dm = reinterpret_cast<BatchMsg*>(h + L.dec_msgs);
   uint64_t* es = reinterpret_cast<uint64_t*>(h + L.enc_start);
   uint64_t* ds = reinterpret_cast<uint64_t*>(h + L.dec_start);
-  fill(em, dm);
+  uint4* eiv = with_ivs ? reinterpret_cast<uint4*>(h + L.enc_iv) : nullptr;
+  uint4* div = with_ivs ? reinterpret_cast<uint4*>(h + L.dec_iv) : nullptr;
+  fill(em, dm, eiv, div);
   uint64_t te = 0, td = 0;
   for (size_t i = 0; i < nenc; ++i) { es[i] = te; te += em[i].nblocks; }
   for (size_t i = 0; i < ndec; ++i) { ds[i] = td; td += dm[i].nblocks; }
@@ -245,10 +250,12 @@ aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
   KernelArgs a{in_base, out_base,
                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.enc_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.enc_start),
                         reinterpret_cast<const uint32_t*>(s.dev + L.enc_warp), te, uint32_t(nenc), 0u,
-                        reinterpret_cast<const uint64_t*>(s.dev + L.enc_gb)},
+                        reinterpret_cast<const uint64_t*>(s.dev + L.enc_gb),
+                        with_ivs ? reinterpret_cast<const uint4*>(s.dev + L.enc_iv) : nullptr},
                BatchDir{reinterpret_cast<const BatchMsg*>(s.dev + L.dec_msgs), reinterpret_cast<const uint64_t*>(s.dev + L.dec_start),
                         reinterpret_cast<const uint32_t*>(s.dev + L.dec_warp), td, uint32_t(ndec), 0u,
-                        reinterpret_cast<const uint64_t*>(s.dev + L.dec_gb)},
+                        reinterpret_cast<const uint64_t*>(s.dev + L.dec_gb),
+                        with_ivs ? reinterpret_cast<const uint4*>(s.dev + L.dec_iv) : nullptr},
                b->pool->entries, uint32_t(ge), {}};
   const cudaKernelNodeParams p = kernel_params(fn, unsigned(G), threads, smem, a);
   if (!s.exec) {  // a later launch with another kernel or shape updates the node in place
@@ -257,7 +264,8 @@ aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
   } else if ((e = cudaGraphExecKernelNodeSetParams(s.exec, s.kernel, &p)) != cudaSuccess) {
     return cuda_error(e, "cudaGraphExecKernelNodeSetParams");
   }
-  if ((e = cudaMemcpyAsync(s.dev, s.host, L.end, cudaMemcpyHostToDevice, b->copy_stream)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(s.dev, s.host, with_ivs ? L.end_iv : L.end, cudaMemcpyHostToDevice, b->copy_stream)) !=
+      cudaSuccess)
     return cuda_error(e, "descriptor upload");
   if ((e = cudaEventRecord(s.copied, b->copy_stream)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
   if ((e = cudaStreamWaitEvent(stream, s.copied, 0)) != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
@@ -271,7 +279,7 @@ aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
 namespace {
 
 aes_status run_locked(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const void* d_in, void* d_out,
-                      size_t buf_bytes, cudaStream_t stream) {
+                      size_t buf_bytes, cudaStream_t stream, const uint8_t* ivs = nullptr) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -298,17 +306,23 @@ aes_status run_locked(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const voi
       return set_error(AES_EINVAL, "message %zu: key slot %u is not loaded", i, m.key_idx);
     (m.dir == AES_ENCRYPT ? nenc : ndec)++;
   }
-  auto fill = [&](BatchMsg* em, BatchMsg* dm) {
+  auto fill = [&](BatchMsg* em, BatchMsg* dm, uint4* eiv, uint4* div) {
     size_t ie = 0, id = 0;
     for (size_t i = 0; i < nmsgs; ++i) {
       const aes_msg& m = msgs[i];
       if (m.length == 0) continue;
       const BatchMsg d{m.key_idx, 0u, m.offset / 16, m.offset / 16, m.length / 16};
-      if (m.dir == AES_ENCRYPT) em[ie++] = d;
-      else dm[id++] = d;
+      if (m.dir == AES_ENCRYPT) {
+        if (eiv) std::memcpy(eiv + ie, ivs + 16 * i, 16);
+        em[ie++] = d;
+      } else {
+        if (div) std::memcpy(div + id, ivs + 16 * i, 16);
+        dm[id++] = d;
+      }
     }
   };
-  return batch_launch_descs(b, nenc, ndec, fill, reinterpret_cast<uint64_t>(d_in), reinterpret_cast<uint64_t>(d_out), stream);
+  return batch_launch_descs(b, nenc, ndec, fill, ivs != nullptr, reinterpret_cast<uint64_t>(d_in),
+                            reinterpret_cast<uint64_t>(d_out), stream);
 }
 
 // The round count every message of each direction has, as batch_launch_descs derives it from
@@ -432,7 +446,7 @@ aes_status aes_batch_create(aes_keypool* pool, size_t max_msgs, aes_batch** out)
   const DeviceInfo* di = current_device_info();
   if (!di) { delete b; return AES_ECUDA; }
   b->wmax = size_t(di->sms) * (kMaxShapeThreads / 32);
-  b->bytes = layout(max_msgs, max_msgs, b->wmax).end;  // enough for any split of max_msgs
+  b->bytes = layout(max_msgs, max_msgs, b->wmax).end_iv;  // enough for any split of max_msgs, with IVs
   if ((e = cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) {
     delete b;
     return cuda_error(e, "cudaStreamCreate");
@@ -458,6 +472,14 @@ aes_status aes_batch_run(aes_batch* b, const aes_msg* msgs, size_t nmsgs, const 
   if (!b) return set_error(AES_EINVAL, "null batch");
   std::lock_guard<std::mutex> lk(b->mu);
   return run_locked(b, msgs, nmsgs, d_in, d_out, buf_bytes, static_cast<cudaStream_t>(cuda_stream));
+}
+
+aes_status aes_batch_run_iv(aes_batch* b, const aes_msg* msgs, const uint8_t* ivs, size_t nmsgs, const void* d_in,
+                            void* d_out, size_t buf_bytes, void* cuda_stream) {
+  clear_error();
+  if (!b) return set_error(AES_EINVAL, "null batch");
+  std::lock_guard<std::mutex> lk(b->mu);
+  return run_locked(b, msgs, nmsgs, d_in, d_out, buf_bytes, static_cast<cudaStream_t>(cuda_stream), ivs);
 }
 
 aes_status aes_batch_set_shape(aes_batch* b, int threads, int blocks_per_lane) {
@@ -526,8 +548,8 @@ aes_status aes_batch_autotune(aes_batch* b, const aes_msg* msgs, size_t nmsgs, c
   return AES_OK;
 }
 
-aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsgs, const void* d_in,
-                             void* d_out, size_t buf_bytes, void* cuda_stream) {
+aes_status aes_crypt_batched_iv(aes_keypool* pool, const aes_msg* msgs, const uint8_t* ivs, size_t nmsgs,
+                                const void* d_in, void* d_out, size_t buf_bytes, void* cuda_stream) {
   clear_error();
   if (!pool || !pool->entries || !pool->mu) return set_error(AES_EINVAL, "null key pool");
   std::lock_guard<std::mutex> lk(*static_cast<std::mutex*>(pool->mu));
@@ -536,7 +558,12 @@ aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsg
     aes_status st = aes_batch_create(pool, std::max<size_t>(nmsgs, 1024), &pool->internal);
     if (st != AES_OK) return st;
   }
-  return aes_batch_run(pool->internal, msgs, nmsgs, d_in, d_out, buf_bytes, cuda_stream);
+  return aes_batch_run_iv(pool->internal, msgs, ivs, nmsgs, d_in, d_out, buf_bytes, cuda_stream);
+}
+
+aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsgs, const void* d_in,
+                             void* d_out, size_t buf_bytes, void* cuda_stream) {
+  return aes_crypt_batched_iv(pool, msgs, nullptr, nmsgs, d_in, d_out, buf_bytes, cuda_stream);
 }
 
 }  // extern "C"

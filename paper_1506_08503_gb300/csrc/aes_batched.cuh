@@ -96,6 +96,23 @@ __device__ __forceinline__ void load_keys(const PoolEntry* pool, uint32_t key, K
   }
 }
 
+__device__ __forceinline__ uint4 ldg_iv(const uint4* p) { return __ldg(p); }
+
+// XORs v into the round key that carries a message's IV: round key 0 for encryption
+// (C = E(P ^ IV)), the last key for decryption (P = D(C) ^ IV; the equivalent inverse
+// cipher's last key is K_0).  On a change of message within one key the old IV is taken out
+// and the new one put in with one XOR of their difference.
+template <int DIR, int NRF>
+__device__ __forceinline__ void fold_iv(KeyRegs<NRF>& k, uint4 v) {
+  uint32_t* w;
+  if constexpr (DIR == AES_ENCRYPT) w = k.kw[0];
+  else if constexpr (NRF == 0) w = k.kl;
+  else w = k.kw[NRF];
+  w[0] ^= v.x; w[1] ^= v.y; w[2] ^= v.z; w[3] ^= v.w;
+}
+
+__device__ __forceinline__ uint4 xor4(uint4 a, uint4 b) { return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w); }
+
 // Rounds 1..nr-1 of one block with the round keys in registers (nr = 10, 12 or 14; the
 // branches are warp-uniform on the fast path).
 template <int DIR>
@@ -167,13 +184,19 @@ __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base
   Cursor c;  // warp-uniform: the message holding block gb
   open_msg(c, bd, bd.warp_msg ? __ldg(bd.warp_msg + w) : find_msg(bd.start, bd.nmsgs, gb));
   load_keys<DIR, NRF>(pool, c.key, k);
+  if (bd.ivs) fold_iv<DIR, NRF>(k, ldg_iv(bd.ivs + c.m));
   constexpr uint32_t kWin = 32u * U;
 
   while (gb < hi) {
     if (gb >= c.end) {
-      const uint32_t old = c.key;
+      const uint32_t old = c.key, oldm = c.m;
       seek(c, bd, gb);
-      if (c.key != old) load_keys<DIR, NRF>(pool, c.key, k);
+      if (c.key != old) {
+        load_keys<DIR, NRF>(pool, c.key, k);
+        if (bd.ivs) fold_iv<DIR, NRF>(k, ldg_iv(bd.ivs + c.m));
+      } else if (bd.ivs) {
+        fold_iv<DIR, NRF>(k, xor4(ldg_iv(bd.ivs + oldm), ldg_iv(bd.ivs + c.m)));
+      }
     }
     uint64_t wend = gb + kWin;
     if (wend > hi) wend = hi;

@@ -111,6 +111,8 @@ static_assert(sizeof(BatchMsg) == 32, "batch descriptors are 32 bytes");
 // kernel runs with exactly the warps the table was made for; warp_gb (optional, nwarps + 1
 // entries) gives each warp's first block, so that the host can balance the slices by work
 // (blocks x rounds) rather than by blocks.  Without it every warp takes an equal block range.
+// ivs (optional, nmsgs entries): message m's IV, XORed into every block of m before the
+// cipher (encryption) or after the inverse cipher (decryption); null means zero IVs.
 struct BatchDir {
   const BatchMsg* msgs;
   const uint64_t* start;
@@ -119,6 +121,7 @@ struct BatchDir {
   uint32_t nmsgs;
   uint32_t pad;
   const uint64_t* warp_gb;
+  const uint4* ivs;
 };
 
 // Kernel arguments: input and output base addresses as integers (the server passes 0 and
@@ -146,11 +149,13 @@ uint64_t work_of(const BatchMsg* m, size_t n, const int8_t* rounds);
 // holding it.
 void weighted_slices(const BatchMsg* m, const uint64_t* start, size_t n, const int8_t* rounds, uint64_t W,
                      uint64_t nw, uint64_t* gb, uint32_t* msg);
-// Launches one batch from descriptors written by `fill(enc, dec)` (nenc and ndec entries,
-// nblocks > 0 each) relative to in_base / out_base.  The caller holds the batch's lock.
-aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec,
-                              const std::function<void(BatchMsg*, BatchMsg*)>& fill, uint64_t in_base,
-                              uint64_t out_base, cudaStream_t stream);
+// Launches one batch from descriptors written by `fill(enc, dec, enc_ivs, dec_ivs)` (nenc and
+// ndec entries, nblocks > 0 each) relative to in_base / out_base; with with_ivs the fill also
+// writes one IV per descriptor (in the same order), else the IV pointers are null.  The
+// caller holds the batch's lock.
+using DescFill = std::function<void(BatchMsg*, BatchMsg*, uint4*, uint4*)>;
+aes_status batch_launch_descs(aes_batch* b, size_t nenc, size_t ndec, const DescFill& fill, bool with_ivs,
+                              uint64_t in_base, uint64_t out_base, cudaStream_t stream);
 }  // namespace aesgb
 
 struct aes_keypool {

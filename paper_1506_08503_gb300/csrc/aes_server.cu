@@ -240,7 +240,7 @@ aes_status issue(aes_server* s, int i) {
   // pass 2 (inside the batch launch): descriptors written straight into the pinned staging.
   // A device destination is the output; a host destination is served from the staging slot,
   // which also holds the input when the source was on the host.
-  auto fill = [&](BatchMsg* em, BatchMsg* dm) {
+  auto fill = [&](BatchMsg* em, BatchMsg* dm, uint4*, uint4*) {
     size_t ie = 0, id = 0;
     for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
       const Req& q = s->at(tk);
@@ -254,7 +254,7 @@ aes_status issue(aes_server* s, int i) {
       else dm[id++] = d;
     }
   };
-  aes_status rc = batch_launch_descs(sl.batch, nenc, ndec, fill, 0, 0, st);
+  aes_status rc = batch_launch_descs(sl.batch, nenc, ndec, fill, false, 0, 0, st);
   if (rc != AES_OK) return rc;
   for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
     const Req& q = s->at(tk);
