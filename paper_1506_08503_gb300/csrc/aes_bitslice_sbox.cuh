@@ -2,191 +2,216 @@
 //
 // Bitsliced AES S-box and inverse S-box: eight 32-bit planes in place, plane i holds bit i of
 // one state byte for 32 blocks.  Derived from the field definition (GF(2^8) inverse followed
-// by the affine map of App. A2; the inverse map of App. A5 followed by the inverse) through
-// the tower GF((2^4)^2); checked by the generator on all 256 inputs.
-//   S-box tower:      zeta = 0xE1 (root of z^4+z+1), lambda = 0xA, eta = 0x42; linear-layer XORs = 34
-//   inverse tower:    zeta = 0xE1, lambda = 0xD, eta = 0x1E; linear-layer XORs = 35
-// Every memory access is absent: the circuit's time does not depend on data or key.
+// by the affine map of App. A2; the inverse map of App. A5 followed by the inverse) through a
+// normal-basis tower GF(((2^2)^2)^2) with 27 AND gates in the two outer products, mapped onto
+// three-input LOP3 instructions by an exact cover; checked by the generator on all 256 inputs.
+//   S-box:          77 LOP3 (117 two-input gates before mapping), N = W^2, L = 0x8, GF(16) inverse as table (tower 104, seed 1010092)
+//   inverse S-box:  77 LOP3 (125 two-input gates before mapping), N = W, L = 0xE, GF(16) inverse as table (tower 14, seed 2001365)
+// No memory access, no branch: the circuit's time does not depend on data or key.
+// Each statement is one three-input table (its LOP3 immediate in the comment), written as a
+// C expression that the compiler folds into that single instruction.
 #pragma once
 #include <cstdint>
+
+#if defined(__CUDACC__)
+#define AES_SBOX_FN __host__ __device__ __forceinline__
+#else
+#define AES_SBOX_FN inline
+#endif
 
 namespace aesgb {
 namespace bs {
 
-template <int LUT>
-__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t d;
-  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
-  return d;
+AES_SBOX_FN void sbox_planes(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint32_t& x4, uint32_t& x5, uint32_t& x6, uint32_t& x7) {
+  const uint32_t i0 = x0;
+  const uint32_t i1 = x1;
+  const uint32_t i2 = x2;
+  const uint32_t i3 = x3;
+  const uint32_t i4 = x4;
+  const uint32_t i5 = x5;
+  const uint32_t i6 = x6;
+  const uint32_t i7 = x7;
+  const uint32_t t9 = i2 ^ i7;  // lop3 0x3C
+  const uint32_t t10 = i4 ^ i7;  // lop3 0x3C
+  const uint32_t t11 = i2 ^ i4;  // lop3 0x3C
+  const uint32_t t12 = i1 ^ (i7 ^ t11);  // lop3 0x96
+  const uint32_t t14 = i2 ^ (i3 ^ t12);  // lop3 0x96
+  const uint32_t t16 = i3 ^ (i6 ^ t12);  // lop3 0x96
+  const uint32_t t17 = i4 ^ (i7 ^ t16);  // lop3 0x96
+  const uint32_t t18 = i0 ^ (t10 ^ t16);  // lop3 0x96
+  const uint32_t t20 = i5 ^ (i6 ^ t17);  // lop3 0x96
+  const uint32_t t21 = i1 ^ (i7 ^ t20);  // lop3 0x96
+  const uint32_t t22 = i1 ^ t21;  // lop3 0x3C
+  const uint32_t t25 = i0 ^ (i5 ^ i6);  // lop3 0x96
+  const uint32_t t27 = i1 ^ (t9 ^ t25);  // lop3 0x96
+  const uint32_t t29 = i5 ^ (i6 ^ t14);  // lop3 0x96
+  const uint32_t t31 = t20 & (i1 ^ i7);  // lop3 0x28
+  const uint32_t t35 = i1 ^ (t31 ^ (i1 | t25));  // lop3 0xA6
+  const uint32_t t37 = i0 & (i4 ^ t25);  // lop3 0x60
+  const uint32_t t38 = t37 ^ (t12 & t14);  // lop3 0x6A
+  const uint32_t t39 = t27 & (i0 ^ t14);  // lop3 0x28
+  const uint32_t t40 = t39 ^ (t12 & t14);  // lop3 0x6A
+  const uint32_t t41 = t11 & (t14 ^ t20);  // lop3 0x60
+  const uint32_t t43 = t41 ^ (t10 & t17);  // lop3 0x6A
+  const uint32_t t45 = t41 ^ (t9 & t29);  // lop3 0x6A
+  const uint32_t t48 = t16 ^ (t40 ^ t43);  // lop3 0x96
+  const uint32_t t49 = t31 ^ (t18 | t22);  // lop3 0x56
+  const uint32_t t50 = t43 ^ (t45 ^ t49);  // lop3 0x96
+  const uint32_t t52 = t21 ^ (t35 ^ t43);  // lop3 0x96
+  const uint32_t t53 = t38 ^ (t43 ^ t45);  // lop3 0x96
+  const uint32_t t54 = t9 ^ (t29 ^ t53);  // lop3 0x96
+  const uint32_t t55 = t50;  // lop3 0xCC
+  const uint32_t t56 = ~((t48 ^ (t50 | t54)));  // lop3 0xE1
+  const uint32_t t57 = t55 ^ (t52 & (t55 ^ t56));  // lop3 0xAC
+  const uint32_t t58 = t50 ^ (t54 & (t50 ^ t52));  // lop3 0xD8
+  const uint32_t t59 = t50 ^ ((t50 ^ t52) & (t52 ^ t54));  // lop3 0xD4
+  const uint32_t t60 = t58 ^ (t48 & (t58 ^ t59));  // lop3 0xAC
+  const uint32_t t61 = t54;  // lop3 0xAA
+  const uint32_t t62 = ~((t52 ^ (t50 | t54)));  // lop3 0xC9
+  const uint32_t t63 = t61 ^ (t48 & (t61 ^ t62));  // lop3 0xAC
+  const uint32_t t64 = t50 ^ (t50 | t54);  // lop3 0x0A
+  const uint32_t t65 = t54 | (t50 ^ t52);  // lop3 0xBE
+  const uint32_t t66 = t64 ^ (t48 & (t64 ^ t65));  // lop3 0xAC
+  const uint32_t t67 = t63 ^ t66;  // lop3 0x3C
+  const uint32_t t69 = t60 ^ t66;  // lop3 0x3C
+  const uint32_t t71 = t57 ^ (t60 ^ t67);  // lop3 0x96
+  const uint32_t t72 = t20 & (t63 ^ t66);  // lop3 0x60
+  const uint32_t t74 = t72 ^ (t18 & t66);  // lop3 0x6A
+  const uint32_t t76 = t72 ^ (t25 & t63);  // lop3 0x6A
+  const uint32_t t77 = t14 & (t57 ^ t60);  // lop3 0x60
+  const uint32_t t79 = t77 ^ (i0 & t60);  // lop3 0x6A
+  const uint32_t t80 = t57 & (i0 ^ t14);  // lop3 0x28
+  const uint32_t t82 = t71 & (t14 ^ t20);  // lop3 0x28
+  const uint32_t t84 = t82 ^ (t17 & t69);  // lop3 0x6A
+  const uint32_t t85 = t29 & (t57 ^ t63);  // lop3 0x60
+  const uint32_t t87 = t67 & (i1 ^ i7);  // lop3 0x28
+  const uint32_t t88 = t66 & (t18 ^ t22);  // lop3 0x28
+  const uint32_t t90 = t63 & (i1 ^ t25);  // lop3 0x28
+  const uint32_t t92 = t12 & (t57 ^ t60);  // lop3 0x60
+  const uint32_t t93 = t60 & (i4 ^ t25);  // lop3 0x28
+  const uint32_t t94 = t92 ^ t93;  // lop3 0x3C
+  const uint32_t t96 = t92 ^ (t27 & t57);  // lop3 0x6A
+  const uint32_t t97 = t71 & (i2 ^ i4);  // lop3 0x28
+  const uint32_t t99 = t97 ^ (t10 & t69);  // lop3 0x6A
+  const uint32_t t100 = t9 & (t57 ^ t63);  // lop3 0x60
+  const uint32_t t103 = t76 ^ (t96 ^ t99);  // lop3 0x96
+  const uint32_t t104 = t77 ^ (t80 ^ t103);  // lop3 0x96
+  const uint32_t t105 = t84 ^ t103;  // lop3 0x3C
+  const uint32_t t107 = t74 ^ (t79 ^ t104);  // lop3 0x96
+  const uint32_t t108 = t87 ^ (t90 ^ t99);  // lop3 0x96
+  const uint32_t t109 = t74 ^ (t79 ^ t108);  // lop3 0x96
+  const uint32_t t110 = t79 ^ (t82 ^ t85);  // lop3 0x96
+  const uint32_t t111 = t87 ^ (t88 ^ t110);  // lop3 0x96
+  const uint32_t t117 = t94 ^ (t103 ^ t111);  // lop3 0x96
+  const uint32_t t118 = t84 ^ (t97 ^ t100);  // lop3 0x96
+  const uint32_t t121 = ~t109;  // lop3 0x0F
+  const uint32_t t122 = ~((t76 ^ (t109 ^ t110)));  // lop3 0x69
+  const uint32_t t123 = ~((t99 ^ (t111 ^ t118)));  // lop3 0x69
+  const uint32_t t124 = ~((t76 ^ (t84 ^ t104)));  // lop3 0x69
+  x0 = t121;
+  x1 = t122;
+  x2 = t117;
+  x3 = t107;
+  x4 = t104;
+  x5 = t123;
+  x6 = t124;
+  x7 = t105;
 }
 
-__device__ __forceinline__ void sbox_planes(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint32_t& x4, uint32_t& x5, uint32_t& x6, uint32_t& x7) {
-  const uint32_t t1 = x4 ^ x5;
-  const uint32_t t2 = x3 ^ x6;
-  const uint32_t t3 = x7 ^ t2;
-  const uint32_t t4 = x0 ^ t1;
-  const uint32_t t5 = x1 ^ x6;
-  const uint32_t t6 = x2 ^ x3;
-  const uint32_t t7 = x2 ^ t3;
-  const uint32_t t8 = x5 ^ x7;
-  const uint32_t t9 = x7 ^ t1;
-  const uint32_t t10 = x0 ^ x5;
-  const uint32_t t11 = x5 ^ t6;
-  const uint32_t t12 = x7 ^ t5;
-  const uint32_t t13 = x1 ^ t3;
-  const uint32_t t14 = x4 ^ t7;
-  const uint32_t t15 = t6 ^ t8;
-  const uint32_t t16 = t1 ^ t5;
-  const uint32_t t17 = t8;
-  const uint32_t t18 = t4 ^ t7;
-  const uint32_t t19 = x7;
-  const uint32_t t20 = t9;
-  const uint32_t t21 = x1 ^ x5 ^ t2;
-  const uint32_t t22 = t4;
-  const uint32_t t23 = x1 ^ t9;
-  const uint32_t t24 = x3 ^ t1;
-  const uint32_t t25 = t3;
-  const uint32_t t26 = (t15 & t13) ^ (t16 & t12) ^ (t17 & t11);
-  const uint32_t t27 = (t16 & t13) ^ (t17 & t12);
-  const uint32_t t28 = (t17 & t13);
-  const uint32_t t29 = (t14 & t10) ^ t26;
-  const uint32_t t30 = (t14 & t11) ^ (t15 & t10) ^ t26 ^ t27;
-  const uint32_t t31 = (t14 & t12) ^ (t15 & t11) ^ (t16 & t10) ^ t27 ^ t28;
-  const uint32_t t32 = (t14 & t13) ^ (t15 & t12) ^ (t16 & t11) ^ (t17 & t10) ^ t28;
-  const uint32_t t33 = t22 ^ t29;
-  const uint32_t t34 = t23 ^ t30;
-  const uint32_t t35 = t24 ^ t31;
-  const uint32_t t36 = t25 ^ t32;
-  const uint32_t t37 = lop3<0x3E>(t33, t34, t35);
-  const uint32_t t38 = lop3<0x49>(t33, t34, t35);
-  const uint32_t t39 = lop3<0xCA>(t36, t38, t37);  // d3 ? f1 : f0
-  const uint32_t t40 = lop3<0xE8>(t33, t34, t35);
-  const uint32_t t41 = lop3<0x1B>(t33, t34, t35);
-  const uint32_t t42 = lop3<0xCA>(t36, t41, t40);  // d3 ? f1 : f0
-  const uint32_t t43 = lop3<0xCA>(t33, t34, t35);
-  const uint32_t t44 = lop3<0x65>(t33, t34, t35);
-  const uint32_t t45 = lop3<0xCA>(t36, t44, t43);  // d3 ? f1 : f0
-  const uint32_t t46 = lop3<0x66>(t33, t34, t35);
-  const uint32_t t47 = lop3<0x87>(t33, t34, t35);
-  const uint32_t t48 = lop3<0xCA>(t36, t47, t46);  // d3 ? f1 : f0
-  const uint32_t t49 = (t15 & t48) ^ (t16 & t45) ^ (t17 & t42);
-  const uint32_t t50 = (t16 & t48) ^ (t17 & t45);
-  const uint32_t t51 = (t17 & t48);
-  const uint32_t t52 = (t14 & t39) ^ t49;
-  const uint32_t t53 = (t14 & t42) ^ (t15 & t39) ^ t49 ^ t50;
-  const uint32_t t54 = (t14 & t45) ^ (t15 & t42) ^ (t16 & t39) ^ t50 ^ t51;
-  const uint32_t t55 = (t14 & t48) ^ (t15 & t45) ^ (t16 & t42) ^ (t17 & t39) ^ t51;
-  const uint32_t t56 = (t19 & t48) ^ (t20 & t45) ^ (t21 & t42);
-  const uint32_t t57 = (t20 & t48) ^ (t21 & t45);
-  const uint32_t t58 = (t21 & t48);
-  const uint32_t t59 = (t18 & t39) ^ t56;
-  const uint32_t t60 = (t18 & t42) ^ (t19 & t39) ^ t56 ^ t57;
-  const uint32_t t61 = (t18 & t45) ^ (t19 & t42) ^ (t20 & t39) ^ t57 ^ t58;
-  const uint32_t t62 = (t18 & t48) ^ (t19 & t45) ^ (t20 & t42) ^ (t21 & t39) ^ t58;
-  const uint32_t t63 = t52 ^ t55;
-  const uint32_t t64 = t60 ^ t61;
-  const uint32_t t65 = t53 ^ t63;
-  const uint32_t t66 = t59 ^ t65;
-  const uint32_t t67 = ~(t66);
-  const uint32_t t68 = ~(t59 ^ t61);
-  const uint32_t t69 = t59 ^ t60 ^ t62;
-  const uint32_t t70 = t59 ^ t52 ^ t54;
-  const uint32_t t71 = t64 ^ t66;
-  const uint32_t t72 = ~(t64 ^ t65);
-  const uint32_t t73 = ~(t63);
-  const uint32_t t74 = t62 ^ t52 ^ t64;
-  x0 = t67;
-  x1 = t68;
-  x2 = t69;
-  x3 = t70;
-  x4 = t71;
-  x5 = t72;
-  x6 = t73;
-  x7 = t74;
-}
-
-__device__ __forceinline__ void inv_sbox_planes(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint32_t& x4, uint32_t& x5, uint32_t& x6, uint32_t& x7) {
-  const uint32_t t1 = x2 ^ x7;
-  const uint32_t t2 = x1 ^ x3;
-  const uint32_t t3 = x4 ^ x5;
-  const uint32_t t4 = x0 ^ x6;
-  const uint32_t t5 = x1 ^ x6;
-  const uint32_t t6 = x3 ^ t1;
-  const uint32_t t7 = x5 ^ x7;
-  const uint32_t t8 = t1 ^ t2;
-  const uint32_t t9 = ~(t8);
-  const uint32_t t10 = ~(x4 ^ t2 ^ t4);
-  const uint32_t t11 = ~(t3 ^ t5);
-  const uint32_t t12 = ~(x2 ^ x5 ^ t5);
-  const uint32_t t13 = ~(x1 ^ t1);
-  const uint32_t t14 = ~(t3 ^ t4);
-  const uint32_t t15 = t3 ^ t8;
-  const uint32_t t16 = t1 ^ t5;
-  const uint32_t t17 = x3;
-  const uint32_t t18 = x5 ^ t2;
-  const uint32_t t19 = ~(x6 ^ t6);
-  const uint32_t t20 = ~(t7);
-  const uint32_t t21 = t4 ^ t6;
-  const uint32_t t22 = ~(t1 ^ t3);
-  const uint32_t t23 = ~(x0 ^ x2);
-  const uint32_t t24 = x6 ^ t7;
-  const uint32_t t25 = (t14 & t12) ^ (t15 & t11) ^ (t16 & t10);
-  const uint32_t t26 = (t15 & t12) ^ (t16 & t11);
-  const uint32_t t27 = (t16 & t12);
-  const uint32_t t28 = (t13 & t9) ^ t25;
-  const uint32_t t29 = (t13 & t10) ^ (t14 & t9) ^ t25 ^ t26;
-  const uint32_t t30 = (t13 & t11) ^ (t14 & t10) ^ (t15 & t9) ^ t26 ^ t27;
-  const uint32_t t31 = (t13 & t12) ^ (t14 & t11) ^ (t15 & t10) ^ (t16 & t9) ^ t27;
-  const uint32_t t32 = t21 ^ t28;
-  const uint32_t t33 = t22 ^ t29;
-  const uint32_t t34 = t23 ^ t30;
-  const uint32_t t35 = t24 ^ t31;
-  const uint32_t t36 = lop3<0x3E>(t32, t33, t34);
-  const uint32_t t37 = lop3<0x49>(t32, t33, t34);
-  const uint32_t t38 = lop3<0xCA>(t35, t37, t36);  // d3 ? f1 : f0
-  const uint32_t t39 = lop3<0xE8>(t32, t33, t34);
-  const uint32_t t40 = lop3<0x1B>(t32, t33, t34);
-  const uint32_t t41 = lop3<0xCA>(t35, t40, t39);  // d3 ? f1 : f0
-  const uint32_t t42 = lop3<0xCA>(t32, t33, t34);
-  const uint32_t t43 = lop3<0x65>(t32, t33, t34);
-  const uint32_t t44 = lop3<0xCA>(t35, t43, t42);  // d3 ? f1 : f0
-  const uint32_t t45 = lop3<0x66>(t32, t33, t34);
-  const uint32_t t46 = lop3<0x87>(t32, t33, t34);
-  const uint32_t t47 = lop3<0xCA>(t35, t46, t45);  // d3 ? f1 : f0
-  const uint32_t t48 = (t14 & t47) ^ (t15 & t44) ^ (t16 & t41);
-  const uint32_t t49 = (t15 & t47) ^ (t16 & t44);
-  const uint32_t t50 = (t16 & t47);
-  const uint32_t t51 = (t13 & t38) ^ t48;
-  const uint32_t t52 = (t13 & t41) ^ (t14 & t38) ^ t48 ^ t49;
-  const uint32_t t53 = (t13 & t44) ^ (t14 & t41) ^ (t15 & t38) ^ t49 ^ t50;
-  const uint32_t t54 = (t13 & t47) ^ (t14 & t44) ^ (t15 & t41) ^ (t16 & t38) ^ t50;
-  const uint32_t t55 = (t18 & t47) ^ (t19 & t44) ^ (t20 & t41);
-  const uint32_t t56 = (t19 & t47) ^ (t20 & t44);
-  const uint32_t t57 = (t20 & t47);
-  const uint32_t t58 = (t17 & t38) ^ t55;
-  const uint32_t t59 = (t17 & t41) ^ (t18 & t38) ^ t55 ^ t56;
-  const uint32_t t60 = (t17 & t44) ^ (t18 & t41) ^ (t19 & t38) ^ t56 ^ t57;
-  const uint32_t t61 = (t17 & t47) ^ (t18 & t44) ^ (t19 & t41) ^ (t20 & t38) ^ t57;
-  const uint32_t t62 = t59 ^ t52;
-  const uint32_t t63 = t60 ^ t51;
-  const uint32_t t64 = t61 ^ t63;
-  const uint32_t t65 = t53 ^ t62;
-  const uint32_t t66 = t58 ^ t62;
-  const uint32_t t67 = t51 ^ t52 ^ t53;
-  const uint32_t t68 = t64;
-  const uint32_t t69 = t52 ^ t54 ^ t64;
-  const uint32_t t70 = t53 ^ t63;
-  const uint32_t t71 = t65;
-  const uint32_t t72 = t59 ^ t60;
-  const uint32_t t73 = t54 ^ t65;
-  x0 = t66;
-  x1 = t67;
-  x2 = t68;
-  x3 = t69;
-  x4 = t70;
-  x5 = t71;
-  x6 = t72;
-  x7 = t73;
+AES_SBOX_FN void inv_sbox_planes(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint32_t& x4, uint32_t& x5, uint32_t& x6, uint32_t& x7) {
+  const uint32_t i0 = x0;
+  const uint32_t i1 = x1;
+  const uint32_t i2 = x2;
+  const uint32_t i3 = x3;
+  const uint32_t i4 = x4;
+  const uint32_t i5 = x5;
+  const uint32_t i6 = x6;
+  const uint32_t i7 = x7;
+  const uint32_t t8 = i1 ^ i4;  // lop3 0x3C
+  const uint32_t t10 = i0 ^ (i3 ^ i7);  // lop3 0x96
+  const uint32_t t11 = i2 ^ t10;  // lop3 0x3C
+  const uint32_t t12 = i2 ^ (t8 ^ t10);  // lop3 0x96
+  const uint32_t t13 = i7 ^ t12;  // lop3 0x3C
+  const uint32_t t14 = i5 ^ t10;  // lop3 0x3C
+  const uint32_t t15 = i0 ^ (i3 ^ i6);  // lop3 0x96
+  const uint32_t t16 = t12 ^ t15;  // lop3 0x3C
+  const uint32_t t19 = i1 ^ (i5 ^ i6);  // lop3 0x96
+  const uint32_t t20 = i0 ^ t19;  // lop3 0x3C
+  const uint32_t t21 = t12 ^ (t15 ^ t20);  // lop3 0x96
+  const uint32_t t24 = i2 ^ (t10 ^ t19);  // lop3 0x96
+  const uint32_t t26 = i1 ^ (i4 ^ t20);  // lop3 0x96
+  const uint32_t t27 = i7 ^ (t8 ^ t24);  // lop3 0x96
+  const uint32_t t28 = i5 ^ (t19 ^ t21);  // lop3 0x96
+  const uint32_t t30 = i0 ^ (i3 ^ t28);  // lop3 0x96
+  const uint32_t t42 = t8 ^ (t8 | t20);  // lop3 0x0C
+  const uint32_t t44 = t42 ^ (t12 & t16);  // lop3 0x6A
+  const uint32_t t46 = t11 ^ (t42 ^ (t11 | t21));  // lop3 0xA6
+  const uint32_t t47 = t27 ^ (t27 | (t14 ^ t20));  // lop3 0x14
+  const uint32_t t49 = t47 ^ (i6 & t13);  // lop3 0x6A
+  const uint32_t t50 = ~((t19 | (i5 ^ t21)));  // lop3 0x21
+  const uint32_t t52 = t14 & (i7 ^ t24);  // lop3 0x48
+  const uint32_t t54 = i7 ^ (t52 ^ (i7 & t10));  // lop3 0x9A
+  const uint32_t t56 = i5 ^ (t52 ^ (i5 | t24));  // lop3 0xA6
+  const uint32_t t59 = t15 ^ (t49 ^ t56);  // lop3 0x96
+  const uint32_t t60 = ~((t26 ^ (t47 ^ t50)));  // lop3 0x69
+  const uint32_t t61 = t54 ^ (t56 ^ t60);  // lop3 0x96
+  const uint32_t t63 = ~((t30 ^ (t44 ^ t56)));  // lop3 0x69
+  const uint32_t t64 = t46 ^ (t54 ^ t56);  // lop3 0x96
+  const uint32_t t65 = ~((t26 ^ (t28 ^ t64)));  // lop3 0x69
+  const uint32_t t66 = t65 | (t59 & t63);  // lop3 0xEA
+  const uint32_t t67 = t63 & (t65 | ~t59);  // lop3 0x8C
+  const uint32_t t68 = t66 ^ (t61 & (t66 ^ t67));  // lop3 0xAC
+  const uint32_t t69 = t65;  // lop3 0xAA
+  const uint32_t t70 = ~((t59 ^ (t61 | t65)));  // lop3 0xE1
+  const uint32_t t71 = t69 ^ (t63 & (t69 ^ t70));  // lop3 0xAC
+  const uint32_t t72 = t59 & (t63 ^ t65);  // lop3 0x60
+  const uint32_t t73 = t59 | ~t65;  // lop3 0xF5
+  const uint32_t t74 = t72 ^ (t61 & (t72 ^ t73));  // lop3 0xAC
+  const uint32_t t75 = t61;  // lop3 0xF0
+  const uint32_t t76 = ~((t63 ^ (t61 | t65)));  // lop3 0xC9
+  const uint32_t t77 = t75 ^ (t59 & (t75 ^ t76));  // lop3 0xAC
+  const uint32_t t79 = t68 ^ t71;  // lop3 0x3C
+  const uint32_t t81 = t68 ^ t74;  // lop3 0x3C
+  const uint32_t t82 = t74 ^ (t77 ^ t79);  // lop3 0x96
+  const uint32_t t83 = t8 ^ (t8 | (t74 ^ t77));  // lop3 0x06
+  const uint32_t t85 = t83 ^ (t12 & t77);  // lop3 0x6A
+  const uint32_t t87 = t11 ^ (t83 ^ (t11 | t74));  // lop3 0xA6
+  const uint32_t t88 = t27 ^ (t27 | t79);  // lop3 0x0C
+  const uint32_t t90 = t88 ^ (t13 & t71);  // lop3 0x6A
+  const uint32_t t92 = t19 ^ (t88 ^ (t19 | t68));  // lop3 0xA6
+  const uint32_t t93 = t82 & (i7 ^ t24);  // lop3 0x28
+  const uint32_t t94 = i7 & (t71 ^ t77);  // lop3 0x60
+  const uint32_t t97 = t93 ^ (t24 & t81);  // lop3 0x6A
+  const uint32_t t98 = t20 & (t74 ^ t77);  // lop3 0x60
+  const uint32_t t100 = t98 ^ (t16 & t77);  // lop3 0x6A
+  const uint32_t t102 = t98 ^ (t21 & t74);  // lop3 0x6A
+  const uint32_t t103 = t79 & (t14 ^ t20);  // lop3 0x28
+  const uint32_t t104 = t71 & ~((i6 ^ t13));  // lop3 0x82
+  const uint32_t t106 = t68 & ~((i5 ^ t21));  // lop3 0x82
+  const uint32_t t108 = t14 & t82;  // lop3 0xC0
+  const uint32_t t109 = t10 ^ (t10 | (t71 ^ t77));  // lop3 0x06
+  const uint32_t t112 = i5 ^ (t108 ^ (i5 | t81));  // lop3 0xA6
+  const uint32_t t114 = t100 ^ (t103 ^ t104);  // lop3 0x96
+  const uint32_t t115 = t90 ^ (t92 ^ t114);  // lop3 0x96
+  const uint32_t t116 = t93 ^ (t94 ^ t115);  // lop3 0x96
+  const uint32_t t117 = t102 ^ (t108 ^ t109);  // lop3 0x96
+  const uint32_t t118 = t103 ^ (t104 ^ t117);  // lop3 0x96
+  const uint32_t t120 = t85 ^ (t87 ^ t115);  // lop3 0x96
+  const uint32_t t122 = t97 ^ (t100 ^ t112);  // lop3 0x96
+  const uint32_t t123 = t85 ^ t122;  // lop3 0x3C
+  const uint32_t t125 = t112 ^ (t117 ^ t120);  // lop3 0x96
+  const uint32_t t127 = t90 ^ (t118 ^ t122);  // lop3 0x96
+  const uint32_t t128 = t102 ^ (t103 ^ t106);  // lop3 0x96
+  const uint32_t t130 = t114 ^ (t116 ^ t128);  // lop3 0x96
+  const uint32_t t132 = t120 ^ (t127 ^ t128);  // lop3 0x96
+  x0 = t125;
+  x1 = t123;
+  x2 = t118;
+  x3 = t130;
+  x4 = t116;
+  x5 = t132;
+  x6 = t120;
+  x7 = t127;
 }
 
 }  // namespace bs
