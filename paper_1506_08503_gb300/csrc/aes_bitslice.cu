@@ -25,8 +25,10 @@ __device__ __forceinline__ void st_block(uint4* p, uint4 v) {
 constexpr int kThreads = 128;
 constexpr int kTile = 1024;  // blocks per warp tile (32 per lane)
 
+// Two CTAs (8 warps) per SM: the 128 planes and the S-box temporaries take up to 255 registers.
+// (Three CTAs, 168 registers, spill and measured slower.)
 template <int NR, int DIR>
-__global__ void __launch_bounds__(kThreads) bs_kernel(const uint4* in, uint4* out, size_t nblocks, const Masks km) {
+__global__ void __launch_bounds__(kThreads, 2) bs_kernel(const uint4* in, uint4* out, size_t nblocks, const Masks km) {
   const unsigned lane = threadIdx.x & 31u;
   const size_t warp = (size_t(blockIdx.x) * kThreads + threadIdx.x) >> 5;
   const size_t nwarps = (size_t(gridDim.x) * kThreads) >> 5;

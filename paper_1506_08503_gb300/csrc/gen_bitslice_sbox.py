@@ -759,8 +759,9 @@ HEADER = """// aes_bitslice_sbox.cuh -- GENERATED by gen_bitslice_sbox.py; do no
 //   S-box:          {fc} LOP3 ({fg} two-input gates before mapping), N = {fn}, L = 0x{fl:X}, GF(16) inverse as {fm} (tower {ft[1]}, seed {ft[3]})
 //   inverse S-box:  {ic} LOP3 ({ig} two-input gates before mapping), N = {inn}, L = 0x{il:X}, GF(16) inverse as {im} (tower {it[1]}, seed {it[3]})
 // No memory access, no branch: the circuit's time does not depend on data or key.
-// Each statement is one three-input table (its LOP3 immediate in the comment), written as a
-// C expression that the compiler folds into that single instruction.
+// Each statement is one three-input table (its LOP3 immediate in the comment), written as a C
+// expression; on the device an empty asm fence after each keeps the compiler from merging
+// tables, so that each folds into that single instruction.
 #pragma once
 #include <cstdint>
 
@@ -769,6 +770,11 @@ HEADER = """// aes_bitslice_sbox.cuh -- GENERATED by gen_bitslice_sbox.py; do no
 #else
 #define AES_SBOX_FN inline
 #endif
+#if defined(__CUDA_ARCH__)
+#define AES_SBOX_FENCE(v) asm("" : "+r"(v))
+#else
+#define AES_SBOX_FENCE(v) ((void)0)
+#endif
 
 namespace aesgb {{
 namespace bs {{
@@ -776,7 +782,35 @@ namespace bs {{
 """
 
 
+def allocate(prog, outs: list[int]) -> tuple[dict, int]:
+    """Registers for the device block's temporaries by a linear scan over the straight-line
+    program: a temporary's register is free again after its last use (outputs stay live to the
+    end).  Returns (node -> register index, number of registers)."""
+    last = {}
+    for k, (v, leaves, t) in enumerate(prog):
+        for l in leaves:
+            last[l] = k
+    for o in outs:
+        last[o] = len(prog)
+    free, reg, nregs = [], {}, 0
+    for k, (v, leaves, t) in enumerate(prog):
+        # operands are read before the result is written, so a register freed here can be reused
+        for l in set(leaves):
+            if l in reg and last[l] == k:
+                free.append(reg[l])
+        if free:
+            reg[v] = free.pop()
+        else:
+            reg[v] = nregs
+            nregs += 1
+    return reg, nregs
+
+
 def render(name: str, prog, outs: list[int]) -> str:
+    """The network as one function: each table is a C expression over its three operands, and
+    on the device its result passes an empty inline-asm fence, so the compiler cannot merge
+    tables (a subexpression shared by two tables would need an instruction of its own) and
+    ptxas folds each into one LOP3 while it schedules them freely; the fence emits nothing."""
     args = ", ".join(f"uint32_t& x{i}" for i in range(8))
     nm = {i: f"i{i}" for i in range(8)}
     lines = [f"  const uint32_t i{i} = x{i};" for i in range(8)]
@@ -784,7 +818,8 @@ def render(name: str, prog, outs: list[int]) -> str:
         nm[v] = f"t{v}"
         ops = [nm[l] for l in leaves]
         ops += [ops[0]] * (3 - len(ops))
-        lines.append(f"  const uint32_t t{v} = {c_expr(lop3_imm(t, len(leaves)), ops)};  // lop3 0x{t:02X}")
+        lines.append(f"  uint32_t t{v} = {c_expr(lop3_imm(t, len(leaves)), ops)};  // lop3 0x{t:02X}")
+        lines.append(f"  AES_SBOX_FENCE(t{v});")
     for i, o in enumerate(outs):
         lines.append(f"  x{i} = {nm[o]};")
     return f"AES_SBOX_FN void {name}({args}) {{\n" + "\n".join(lines) + "\n}\n\n"
