@@ -319,6 +319,11 @@ void issuer_main(aes_server* s, int i) {
 }
 
 constexpr uint64_t kInlineIssue = 256;  // batches up to this many requests skip the hand-off
+// With no batch on the GPU, batches ramp up: at most kRampBatch requests while no slot is busy,
+// four times that with one busy, and so on up to max_batch.  A burst arriving at an idle server
+// then reaches the GPU after a small batch's host work instead of a full batch's (descriptor
+// building is linear in the batch), and later batches are prepared while earlier ones run.
+constexpr uint64_t kRampBatch = 512;
 
 // The worker admits queued requests into batches and retires finished batches.  While a
 // batch is in flight it does not sleep: it polls the batches' done events between admissions
@@ -362,9 +367,13 @@ void worker_main(aes_server* s) {
       continue;
     }
     // 2. admit from the head of the queue into one batch: the ticket range [admit, t)
+    uint64_t limit = kRampBatch;
+    for (const StreamSlot& o : s->slots)
+      if (o.busy && limit < s->cfg.max_batch) limit *= 4;
+    if (limit > s->cfg.max_batch) limit = s->cfg.max_batch;
     const uint64_t first = s->admit;
     uint64_t t = first;
-    while (t < s->filled && t - first < s->cfg.max_batch && s->inflight < s->cfg.max_inflight) {
+    while (t < s->filled && t - first < limit && s->inflight < s->cfg.max_inflight) {
       Req& q = s->at(t);
       if (needs_staging(s, q.r)) {
         size_t off = 0;
