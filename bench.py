@@ -110,6 +110,7 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     p.add_argument("--nblocks", type=int, default=NBLOCKS, help="blocks per rank (default 2^26 = 1 GiB)")
     p.add_argument("--no-batched", action="store_true", help="skip the 4096-message batched measurement")
+    p.add_argument("--no-bitsliced", action="store_true", help="skip the bitsliced kernel's 1 GiB measurement")
     p.add_argument("--tt-shape", default=None,
                    help="T,U: set the AUTO kernel to the T-table kernel with this CTA size and blocks per "
                         "thread instead of running the launch tuner (for profiling)")
@@ -321,7 +322,7 @@ def summary_of(line: dict, sms: int) -> dict:
     c = line.get("cbc")
     if c:
         s["cbc"] = [{"msgs": row["messages"], "blocks": row["blocks_per_message"], "enc_gbs": row["encrypt_gbs"],
-                     "dec_gbs": row["decrypt_gbs"]} for row in c["rows"]]
+                     "dec_gbs": row["decrypt_gbs"]} for row in c["rows"] + [c["varying_lengths_own_keys"]]]
     v = line.get("served")
     if v:
         cl = v["closed_loop"]
@@ -436,7 +437,38 @@ def measure_cbc(aes, torch, dev) -> dict:
         if not torch.equal(z, x):
             raise RuntimeError("CBC round trip failed")
         rows.append(entry)
-    return {"mode": "CBC over whole messages, AES-128, one IV per message", "rows": rows}
+    out = {"mode": "CBC over whole messages, AES-128, one IV per message", "rows": rows}
+    # the general form through aes_cbc_batched: 128 messages of lengths 1 .. 4096 blocks
+    # (geometric), each with its own AES-128 key and IV
+    rng = np.random.default_rng(5)
+    n = 128
+    lengths = np.resize(np.unique(np.geomspace(1, 4096, n).astype(np.int64)), n) * 16
+    offs = np.concatenate([[0], np.cumsum(lengths)[:-1]]).astype(np.int64)
+    total = int(lengths.sum())
+    msgs = np.zeros(n, dtype=aes.msg_dtype())
+    msgs["key_idx"], msgs["offset"], msgs["length"] = np.arange(n), offs, lengths
+    ivs = rng.integers(0, 256, (n, 16), dtype=np.uint8)
+    with aes.KeyPool(n) as pool:
+        pool.load_keys(0, rng.integers(0, 256, (n, 16), dtype=np.uint8), 128)
+        x = torch.randint(0, 256, (total,), dtype=torch.uint8, device=dev)
+        y, z = torch.empty_like(x), torch.empty_like(x)
+        entry = {"messages": n, "blocks_per_message": "1..4096 (geometric)", "bytes": total,
+                 "api": "aes_cbc_batched (own key and IV per message)"}
+        for d, src, dst in (("encrypt", x, y), ("decrypt", y, z)):
+            msgs["dir"] = 0 if d == "encrypt" else 1
+            for _ in range(2):
+                aes.aes_cbc_batched(pool, msgs, ivs, src.data_ptr(), dst.data_ptr(), total)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                aes.aes_cbc_batched(pool, msgs, ivs, src.data_ptr(), dst.data_ptr(), total)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            entry[d + "_gbs"] = total / (e0.elapsed_time(e1) / 5 / 1e3) / 1e9
+        if not torch.equal(z, x):
+            raise RuntimeError("batched CBC round trip failed")
+        out["varying_lengths_own_keys"] = entry
+    return out
 
 
 def measure_small_latency(aes, torch, dev) -> dict:
@@ -860,7 +892,7 @@ def run_ours(args):
                     "decrypt_gbs_best": n * 16 / (min(ip_dec) / 1e3) / 1e9, "repetitions": 10}
 
     bitsliced = None
-    if extras and args.kernel != "bitslice":
+    if extras and args.kernel != "bitslice" and not args.no_bitsliced:
         bitsliced = measure_bitsliced(aes, torch, dev, x, n, key, sms)
 
     batched = None

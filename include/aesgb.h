@@ -289,6 +289,20 @@ aes_status aes_crypt_batched(aes_keypool* pool, const aes_msg* msgs, size_t nmsg
 aes_status aes_crypt_batched_iv(aes_keypool* pool, const aes_msg* msgs, const uint8_t* ivs, size_t nmsgs,
                                 const void* d_in, void* d_out, size_t buf_bytes, void* cuda_stream);
 
+/* The paper's CBC mode in its general form (Section II: key tensor K with a schedule per message,
+ * IV matrix V with a row per message; App. A1/A4): many messages of different lengths, message i
+ * under key-pool slot msgs[i].key_idx and IV ivs[16 i .. 16 i + 15] (host array of nmsgs x 16
+ * bytes; NULL means zero IVs), chained over its blocks: C_j = Cipher_K(P_j xor C_{j-1}) with
+ * C_{-1} = IV for msgs[i].dir = AES_ENCRYPT, P_j = InvCipher_K(C_j) xor C_{j-1} for AES_DECRYPT.
+ * msgs and the buffers follow aes_batch_run's rules (offsets index both buffers, whole blocks,
+ * AES-128/192/256 keys mixed).  Encryption runs one lane per message (a chain is serial, so a
+ * long message is as slow as its chain); decryption runs one lane per block.  A call with any
+ * decryption message cannot run in place (AES_EINVAL).  Asynchronous on cuda_stream; the first
+ * call on a pool allocates its descriptor buffers (kept with the pool, grown as needed).
+ * Calls on one pool are serialised. */
+aes_status aes_cbc_batched(aes_keypool* pool, const aes_msg* msgs, const uint8_t* ivs, size_t nmsgs, const void* d_in,
+                           void* d_out, size_t buf_bytes, void* cuda_stream);
+
 /* Batched encryption/decryption for callers that may not allocate device memory: for
  * example a plug-in whose host application owns all device memory and only lends it input
  * and output buffers, or a latency-critical path that cannot afford cudaMalloc's implicit

@@ -131,6 +131,7 @@ _SIGS: dict[str, tuple] = {
     "aes_batch_destroy": (_I, [_VP]),
     "aes_crypt_batched": (_I, [_VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "aes_crypt_batched_iv": (_I, [_VP, _VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
+    "aes_cbc_batched": (_I, [_VP, _VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "aes_server_create": (_I, [ctypes.POINTER(aes_server_cfg), _VP, ctypes.POINTER(_VP)]),
     "aes_server_submit": (_I, [_VP, ctypes.POINTER(aes_request), ctypes.POINTER(ctypes.c_uint64)]),
     "aes_server_submit_many": (_I, [_VP, _VP, _SZ, _VP]),
@@ -487,6 +488,15 @@ def _ivs_array(ivs, n: int):
     if v.size != 16 * n:
         raise ValueError("ivs must hold 16 bytes per message")
     return v
+
+
+def aes_cbc_batched(pool: KeyPool, msgs, ivs, d_in: int, d_out: int, buf_bytes: int, stream=None) -> None:
+    """CBC chained over each message (its own key slot and IV; ivs: host uint8, len(msgs) x 16,
+    or None for zero IVs)."""
+    a, p, n = _msgs_ptr(msgs)
+    v = None if ivs is None else _ivs_array(ivs, n)
+    _check(lib().aes_cbc_batched(pool.handle, p, None if v is None else v.ctypes.data, n, d_in, d_out, buf_bytes,
+                                 _stream_ptr(stream)))
 
 
 def aes_crypt_batched_iv(pool: KeyPool, msgs, ivs, d_in: int, d_out: int, buf_bytes: int, stream=None) -> None:

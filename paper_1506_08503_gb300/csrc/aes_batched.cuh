@@ -159,9 +159,15 @@ __device__ __forceinline__ uint4 crypt_keys(uint4 v, const KeyRegs<NRF>& k, cons
 // The work of CTA `cta` of the `ncta` CTAs given to one direction.
 // NRF != 0: every message of the direction has NRF rounds (the host checks), so the round
 // loop is fixed and the keys take NRF + 1 rows of registers.
-template <int DIR, int THREADS, int U, int NRF = 0>
+// CHAIN (decryption only): the paper's CBC over whole messages, P_j = D(C_j) ^ C_{j-1} with
+// C_{-1} = the message's IV (App. A4): each block's output is XORed with the previous input
+// block of its message, or with bd.ivs[m] for the message's first block, instead of the IV
+// riding on the keys.  The blocks are read through L1, so that the previous block, read by
+// the neighbouring lane in the same window, is mostly an L1 hit.
+template <int DIR, int THREADS, int U, int NRF = 0, bool CHAIN = false>
 __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base, const BatchDir& bd,
                                              const PoolEntry* pool, uint32_t cta, uint32_t ncta, uint32_t* smem) {
+  static_assert(!CHAIN || DIR == AES_DECRYPT, "chaining is for decryption only");
   if (bd.total == 0) return;  // CTA-uniform, before any barrier
   fill_tables<DIR>(smem);
   __syncthreads();
@@ -184,7 +190,7 @@ __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base
   Cursor c;  // warp-uniform: the message holding block gb
   open_msg(c, bd, bd.warp_msg ? __ldg(bd.warp_msg + w) : find_msg(bd.start, bd.nmsgs, gb));
   load_keys<DIR, NRF>(pool, c.key, k);
-  if (bd.ivs) fold_iv<DIR, NRF>(k, ldg_iv(bd.ivs + c.m));
+  if (!CHAIN && bd.ivs) fold_iv<DIR, NRF>(k, ldg_iv(bd.ivs + c.m));
   constexpr uint32_t kWin = 32u * U;
 
   while (gb < hi) {
@@ -193,8 +199,8 @@ __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base
       seek(c, bd, gb);
       if (c.key != old) {
         load_keys<DIR, NRF>(pool, c.key, k);
-        if (bd.ivs) fold_iv<DIR, NRF>(k, ldg_iv(bd.ivs + c.m));
-      } else if (bd.ivs) {
+        if (!CHAIN && bd.ivs) fold_iv<DIR, NRF>(k, ldg_iv(bd.ivs + c.m));
+      } else if (!CHAIN && bd.ivs) {
         fold_iv<DIR, NRF>(k, xor4(ldg_iv(bd.ivs + oldm), ldg_iv(bd.ivs + c.m)));
       }
     }
@@ -208,7 +214,18 @@ __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t i = u * 32u + lane;
-      v[u] = i < cnt ? ld_block(src + i) : make_uint4(0u, 0u, 0u, 0u);
+      if constexpr (CHAIN) v[u] = i < cnt ? __ldg(src + i) : make_uint4(0u, 0u, 0u, 0u);
+      else v[u] = i < cnt ? ld_block(src + i) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    uint4 prev[CHAIN ? U : 1];
+    if constexpr (CHAIN) {
+      const bool first = gb == c.start;  // the window starts at the message's first block
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t i = u * 32u + lane;
+        prev[u] = i >= cnt ? make_uint4(0u, 0u, 0u, 0u)
+                  : (first && i == 0) ? ldg_iv(bd.ivs + c.m) : __ldg(src + i - 1);
+      }
     }
     // the next window of the same message goes to L2 while this one is enciphered
     uint64_t nend = wend + kWin;
@@ -239,6 +256,10 @@ __device__ __forceinline__ void batched_body(uint64_t in_base, uint64_t out_base
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) v[u] = crypt_keys<DIR, NRF>(v[u], k, sm, lc);
+    if constexpr (CHAIN) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = xor4(v[u], prev[u]);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t i = u * 32u + lane;

@@ -166,5 +166,11 @@ struct aes_keypool {
   size_t raw_cap = 0;                   // bytes
   int8_t* nr = nullptr;                 // host shadow: rounds per slot (0 = empty)
   aes_batch* internal = nullptr;        // for aes_crypt_batched
-  void* mu = nullptr;                   // std::mutex*, serialises aes_crypt_batched
+  void* mu = nullptr;                   // std::mutex*, serialises aes_crypt_batched and aes_cbc_batched
+  void* cbc = nullptr;                  // descriptor buffers of aes_cbc_batched (aes_cbc_batched.cu)
 };
+
+namespace aesgb {
+// Frees the pool's aes_cbc_batched buffers (called by aes_keypool_destroy).
+void cbc_batched_release(aes_keypool* pool);
+}  // namespace aesgb

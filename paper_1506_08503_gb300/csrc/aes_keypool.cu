@@ -170,6 +170,7 @@ aes_status aes_keypool_destroy(aes_keypool* pool) {
   clear_error();
   if (!pool) return AES_OK;
   if (pool->internal) aes_batch_destroy(pool->internal);
+  aesgb::cbc_batched_release(pool);
   if (pool->entries) cudaFree(pool->entries);
   if (pool->raw) cudaFree(pool->raw);
   delete[] pool->nr;

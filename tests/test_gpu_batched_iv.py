@@ -1,8 +1,10 @@
-"""GPU parity of the batched launch with one IV per message (the IV matrix V of the paper's
+"""GPU parity of the batched paths with one IV per message (the IV matrix V of the paper's
 Section II, one row per message, with the key tensor K's schedule per message), through the C
-ABI (aes_crypt_batched_iv, aes_batch_run_iv), against the CPU oracle: every block of message
-i is C = Cipher_Ki(P ^ IV_i), and decryption P = InvCipher_Ki(C) ^ IV_i (App. A1/A4 with one
-block per message).  Bit-exact, message by message.
+ABI, against the CPU oracle, bit-exact, message by message:
+  * aes_crypt_batched_iv / aes_batch_run_iv: every block of message i is a one-block CBC
+    message, C = Cipher_Ki(P ^ IV_i), and decryption P = InvCipher_Ki(C) ^ IV_i;
+  * aes_cbc_batched: the paper's CBC chained over each whole message (App. A1/A4),
+    C_j = Cipher_Ki(P_j ^ C_{j-1}) with C_{-1} = IV_i.
 """
 import os
 
@@ -116,3 +118,87 @@ def test_iv_array_size_is_checked(aes_lib_ready):
         msgs = np.zeros(2, dtype=aes.msg_dtype())
         with pytest.raises(ValueError):
             aes.aes_crypt_batched_iv(pool, msgs, np.zeros(16, dtype=np.uint8), 0, 0, 0)
+
+
+def _cbc_expect(orc, keys, key_idx, dirs, ivs, offsets, lengths, data):
+    out = data.copy()
+    for i in range(len(lengths)):
+        o, L = int(offsets[i]), int(lengths[i])
+        if not L:
+            continue
+        iv = ivs[i] if ivs is not None else np.zeros(16, np.uint8)
+        f = orc.cbc_decrypt if dirs[i] else orc.cbc_encrypt
+        out[o:o + L] = f(keys[int(key_idx[i])], iv, data[o:o + L])
+    return out
+
+
+@pytest.mark.parametrize("with_ivs", [True, False])
+def test_cbc_chained_messages_own_keys_and_ivs(aes_lib_ready, orc, with_ivs):
+    """The paper's CBC over whole messages in its general form (aes_cbc_batched): lognormal
+    lengths, AES-128/192/256 keys, each message with its own key and IV, both directions in one
+    call, empty messages; every message against the oracle's CBC, and decryption of the
+    ciphertext restores the plaintext."""
+    import torch
+
+    rng = np.random.default_rng(80 + with_ivs)
+    n = 400
+    keys = [rng.integers(0, 256, b // 8, dtype=np.uint8) for b in (128, 192, 256) for _ in range(5)]
+    key_idx = rng.integers(0, len(keys), n).astype(np.uint32)
+    dirs = rng.integers(0, 2, n).astype(np.uint32)
+    m = workloads.batched_messages(81, m=n, median=512.0, hi=1 << 16)
+    lengths = m.lengths.copy()
+    lengths[::37] = 0
+    ivs = rng.integers(0, 256, (n, 16), dtype=np.uint8) if with_ivs else None
+    msgs = np.zeros(n, dtype=aes.msg_dtype())
+    msgs["key_idx"], msgs["dir"], msgs["offset"], msgs["length"] = key_idx, dirs, m.offsets, lengths
+    want = _cbc_expect(orc, keys, key_idx, dirs, ivs, m.offsets, lengths, m.data)
+    with aes.KeyPool(len(keys)) as pool:
+        for i, k in enumerate(keys):
+            pool.load_keys(i, k[None, :], 8 * len(k))
+        x = dev(m.data)
+        y = x.clone()
+        aes.aes_cbc_batched(pool, msgs, ivs, x.data_ptr(), y.data_ptr(), m.data.size)
+        assert np.array_equal(host(y), want)
+        # the encrypted messages decrypt back (all messages decrypted this time)
+        enc = msgs["dir"] == 0
+        back = msgs.copy()
+        back["dir"] = 1
+        back["length"] = np.where(enc, msgs["length"], 0)
+        z = y.clone()
+        aes.aes_cbc_batched(pool, back, ivs, y.data_ptr(), z.data_ptr(), m.data.size)
+        zz = host(z)
+        for i in np.nonzero(enc & (lengths > 0))[0]:
+            o, L = int(m.offsets[i]), int(lengths[i])
+            assert np.array_equal(zz[o:o + L], m.data[o:o + L]), i
+
+
+def test_cbc_128_messages_of_varying_length(aes_lib_ready, orc):
+    """The paper's second workload shape (Section IV, Fig. 3): 128 messages of lengths from one
+    block to 4096 blocks, one AES-128 key and IV each, encrypted and decrypted."""
+    import torch
+
+    rng = np.random.default_rng(82)
+    n = 128
+    lengths = (np.unique(np.geomspace(1, 4096, n).astype(np.int64), return_counts=False))
+    lengths = np.resize(lengths, n) * 16
+    offsets = np.concatenate([[0], np.cumsum(lengths)[:-1]]).astype(np.int64)
+    data = rng.integers(0, 256, int(lengths.sum()), dtype=np.uint8)
+    keys = rng.integers(0, 256, (n, 16), dtype=np.uint8)
+    ivs = rng.integers(0, 256, (n, 16), dtype=np.uint8)
+    msgs = np.zeros(n, dtype=aes.msg_dtype())
+    msgs["key_idx"], msgs["offset"], msgs["length"] = np.arange(n), offsets, lengths
+    with aes.KeyPool(n) as pool:
+        pool.load_keys(0, keys, 128)
+        x = dev(data)
+        y = torch.empty_like(x)
+        aes.aes_cbc_batched(pool, msgs, ivs, x.data_ptr(), y.data_ptr(), data.size)
+        ct = host(y)
+        for i in range(n):
+            o, L = int(offsets[i]), int(lengths[i])
+            assert np.array_equal(ct[o:o + L], orc.cbc_encrypt(keys[i], ivs[i], data[o:o + L])), i
+        msgs["dir"] = 1
+        z = torch.empty_like(x)
+        aes.aes_cbc_batched(pool, msgs, ivs, y.data_ptr(), z.data_ptr(), data.size)
+        assert torch.equal(z, x)
+        with pytest.raises(aes.AesError):  # decryption in place is refused
+            aes.aes_cbc_batched(pool, msgs, ivs, y.data_ptr(), y.data_ptr(), data.size)
