@@ -107,11 +107,21 @@ BS_FN constexpr int isr_src(int r, int c) { return r + 4 * ((c - r) & 3); }
 // so out_r bit i is a three-input XOR for i = 0, 2, 5, 6, 7 and two for i = 1, 3, 4:
 // 19 instructions per row.
 BS_FN void mix_column(const uint32_t* const (&a)[4], const uint32_t* cm, uint32_t* const (&o)[4]) {
+  uint32_t c[32];  // the column's folding constants, read as eight 16-byte vectors on the device
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint4 v = reinterpret_cast<const uint4*>(cm)[q];
+    c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+  }
+#else
+  for (int i = 0; i < 32; ++i) c[i] = cm[i];
+#endif
   uint32_t t[4][8];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int i = 0; i < 8; ++i) t[r][i] = xor3(a[r][i], a[(r + 1) & 3][i], cm[8 * r + i]);
+    for (int i = 0; i < 8; ++i) t[r][i] = xor3(a[r][i], a[(r + 1) & 3][i], c[8 * r + i]);
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const uint32_t* u = t[r];
@@ -207,28 +217,36 @@ BS_FN void inv_shift(const uint32_t* s, uint32_t* n) {
       for (int i = 0; i < 8; ++i) n[8 * (r + 4 * c) + i] = s[8 * isr_src(r, c) + i];
 }
 
-// Masks row r: round 0 = K_0 (+ IV), rows 1..Nr-1 = the folding constants of K_r, row Nr = K_Nr.
+// Masks row r (km + 128 r): round 0 = K_0 (+ IV), rows 1..Nr-1 = the folding constants of
+// K_r, row Nr = K_Nr.  The middle rounds run as a loop, not unrolled: sixteen S-box networks
+// and a MixColumns are some 1,600 instructions per round, and the whole cipher unrolled
+// (25,000 for AES-128) would not stay in the instruction caches (8 warps per SM streaming
+// through it stalled on instruction fetch more than on anything else).
 template <int NR>
-BS_FN void encrypt_planes(uint32_t* s, const Masks& km) {
-  ark(s, km.m[0]);
-#pragma unroll
-  for (int r = 1; r <= NR; ++r) {
+BS_FN void encrypt_planes(uint32_t* s, const uint32_t* km) {
+  ark(s, km);
+#pragma unroll 1
+  for (int r = 1; r < NR; ++r) {
     sub_bytes(s);
     uint32_t n[128];
-    if (r < NR) shift_mix(s, n, km.m[r]);
-    else shift_ark(s, n, km.m[NR]);
+    shift_mix(s, n, km + 128 * r);
 #pragma unroll
     for (int i = 0; i < 128; ++i) s[i] = n[i];
   }
+  sub_bytes(s);
+  uint32_t n[128];
+  shift_ark(s, n, km + 128 * NR);
+#pragma unroll
+  for (int i = 0; i < 128; ++i) s[i] = n[i];
 }
 
 // The paper's inverse cipher order (App. A4): for r = Nr..1 add K_r, InvMixColumns unless
 // r = Nr, InvShiftRows, InvSubBytes; then add K_0 (which carries the IV).  For r < Nr the key
 // addition rides inside InvMixColumns (masks row r = the folding constants of
-// InvMixColumns(K_r)).
+// InvMixColumns(K_r)).  The middle rounds run as a loop, as in encrypt_planes.
 template <int NR>
-BS_FN void decrypt_planes(uint32_t* s, const Masks& km) {
-  ark(s, km.m[NR]);
+BS_FN void decrypt_planes(uint32_t* s, const uint32_t* km) {
+  ark(s, km + 128 * NR);
   {
     uint32_t n[128];
     inv_shift(s, n);
@@ -236,21 +254,21 @@ BS_FN void decrypt_planes(uint32_t* s, const Masks& km) {
     for (int i = 0; i < 128; ++i) s[i] = n[i];
   }
   inv_sub_bytes(s);
-#pragma unroll
+#pragma unroll 1
   for (int r = NR - 1; r >= 1; --r) {
     uint32_t n[128];
-    inv_mix_shift(s, n, km.m[r]);
+    inv_mix_shift(s, n, km + 128 * r);
 #pragma unroll
     for (int i = 0; i < 128; ++i) s[i] = n[i];
     inv_sub_bytes(s);
   }
-  ark(s, km.m[0]);
+  ark(s, km);
 }
 
 // One tile: words[32 w + j] is word w (bytes 4w..4w+3) of block j, in and out.  Four 32x32
 // transposes turn the 32 blocks into 128 planes and back around the rounds.
 template <int NR, int DIR>
-BS_FN void crypt_tile(uint32_t* s, const Masks& km) {
+BS_FN void crypt_tile(uint32_t* s, const uint32_t* km) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) transpose32(s + 32 * q);
   if constexpr (DIR == AES_ENCRYPT) encrypt_planes<NR>(s, km);

@@ -18,7 +18,7 @@ void run(const aesgb::bs::Masks& km, const uint8_t* in, uint8_t* out, size_t nbl
         if (t + j < nblocks) std::memcpy(&v, in + 16 * (t + j) + 4 * w, 4);  // little-endian words
         s[32 * w + j] = v;
       }
-    aesgb::bs::crypt_tile<NR, DIR>(s, km);
+    aesgb::bs::crypt_tile<NR, DIR>(s, km.m[0]);
     for (int j = 0; j < 32 && t + j < nblocks; ++j)
       for (int w = 0; w < 4; ++w) std::memcpy(out + 16 * (t + j) + 4 * w, &s[32 * w + j], 4);
   }
