@@ -483,42 +483,40 @@ def measure_small_latency(aes, torch, dev) -> dict:
     """The oracle-sized case: 4096 blocks (64 KiB, seed 0) encrypted then decrypted, one call at a
     time on an idle GPU; this fits in L2 and is bound by launch latency, so it is reported in
     microseconds (median over 200 calls, CUDA events around each call: through the Python
-    binding, and as a replayed CUDA graph of the same call)."""
+    binding, and as a replayed CUDA graph of the same call).  AES_IMPL_AUTO takes the small-call
+    kernel (tables from global memory); the shared-memory T-table kernel is timed beside it."""
     w = workloads.plain(0, 4096)
     ks = aes.aes_key_expand(w.key.tobytes())
     x = torch.from_numpy(w.data).to(dev)
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
     out = {}
+
+    def per_call(fn):
+        times = []
+        for k in range(210):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 10:
+                times.append(e0.elapsed_time(e1) * 1e3)
+        return statistics.median(times)
+
     for d, src, dst in (("encrypt", x, y), ("decrypt", y, x)):
-        times = []
-        for k in range(210):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            aes.aes_crypt_blocks(ks, None, src.data_ptr(), dst.data_ptr(), 4096, d, "ttable")
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if k >= 10:
-                times.append(e0.elapsed_time(e1) * 1e3)
-        out[d + "_us_median"] = statistics.median(times)
-        # the same call captured once in a CUDA graph and replayed: the device-side latency,
-        # without the Python and ctypes path in front of the launch
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            aes.aes_crypt_blocks(ks, None, src.data_ptr(), dst.data_ptr(), 4096, d, "ttable")
-        times = []
-        for k in range(210):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            g.replay()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if k >= 10:
-                times.append(e0.elapsed_time(e1) * 1e3)
-        out[d + "_graph_replay_us_median"] = statistics.median(times)
-        del g
+        for impl, tag in (("auto", ""), ("ttable", "_smem_ttable")):
+            call = (lambda s=src, t=dst, dd=d, i=impl:
+                    aes.aes_crypt_blocks(ks, None, s.data_ptr(), t.data_ptr(), 4096, dd, i))
+            out[d + tag + "_us_median"] = per_call(call)
+            # the same call captured once in a CUDA graph and replayed: the device-side latency,
+            # without the Python and ctypes path in front of the launch
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                call()
+            out[d + tag + "_graph_replay_us_median"] = per_call(g.replay)
+            del g
     if not torch.equal(x, torch.from_numpy(w.data).to(dev)):
         raise RuntimeError("4096-block round trip failed")
     out["workload"] = "4096 blocks (64 KiB), AES-128, seed 0"

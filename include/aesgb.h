@@ -90,7 +90,10 @@ aes_status aes_decrypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, con
 /* Same, with the direction (AES_ENCRYPT / AES_DECRYPT) and kernel family (AES_IMPL_*)
  * chosen explicitly.  An unknown dir or impl is AES_EINVAL.  AES_IMPL_AUTO takes the choice
  * aes_autotune_blocks made for this device, direction and round count, else the T-tables
- * with 512-thread CTAs and two blocks in flight per thread. */
+ * with 512-thread CTAs and two blocks in flight per thread; calls of at most 32768 blocks
+ * take a T-table kernel that reads its tables from global memory through the read-only cache
+ * (no per-CTA fill of shared-memory tables: a small call's latency), unless
+ * aes_set_auto_choice has pinned the choice. */
 aes_status aes_crypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, const void* d_in,
                             void* d_out, size_t nblocks, int dir, int impl, void* cuda_stream);
 
@@ -109,7 +112,10 @@ aes_status aes_autotune_blocks(const aes_key_schedule* ks, const void* d_in, voi
 
 /* Sets the AES_IMPL_AUTO choice for the current device, `dir` and round count `nr` (10, 12,
  * 14) directly, without timing: impl AES_IMPL_TTABLE with one of the (threads, unroll) pairs
- * aes_autotune_blocks tries, or AES_IMPL_BITSLICE with (128, 32).  AES_EINVAL otherwise. */
+ * aes_autotune_blocks tries, or AES_IMPL_BITSLICE with (128, 32).  AES_EINVAL otherwise.  The
+ * choice is pinned: it serves AES_IMPL_AUTO calls of every size, small calls included.
+ * impl = AES_IMPL_AUTO (threads and unroll ignored) clears the tuned or pinned choice, back to
+ * the default. */
 aes_status aes_set_auto_choice(int dir, int nr, int impl, int threads, int unroll);
 
 /* The paper's CBC mode over whole messages (Section II; App. A1 encryption, App. A4

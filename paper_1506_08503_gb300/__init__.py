@@ -293,8 +293,9 @@ def aes_autotune_blocks(ks: aes_key_schedule, d_in: int, d_out: int, nblocks: in
 
 
 def aes_set_auto_choice(dir, nr: int, impl, threads: int, blocks_per_thread: int) -> None:
-    """Sets the AES_IMPL_AUTO kernel for this device, direction and round count directly."""
-    code = {"ttable": AES_IMPL_TTABLE, "bitslice": AES_IMPL_BITSLICE}.get(impl, impl)
+    """Sets (pins) the AES_IMPL_AUTO kernel for this device, direction and round count directly;
+    impl "auto" clears it back to the default."""
+    code = {"auto": AES_IMPL_AUTO, "ttable": AES_IMPL_TTABLE, "bitslice": AES_IMPL_BITSLICE}.get(impl, impl)
     _check(lib().aes_set_auto_choice(_dir(dir), nr, int(code), threads, blocks_per_thread))
 
 

@@ -208,7 +208,15 @@ aes_status aes_crypt_blocks(const aes_key_schedule* ks, const uint8_t* iv, const
     return set_error(AES_EINVAL, "input and output overlap without being identical");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   TTConfig cfg;
-  if (impl == AES_IMPL_AUTO && !tuned_choice(dir, ks->nr, &impl, &cfg)) impl = AES_IMPL_TTABLE;
+  if (impl == AES_IMPL_AUTO) {
+    bool pinned = false;
+    if (!tuned_choice(dir, ks->nr, &impl, &cfg, &pinned)) impl = AES_IMPL_TTABLE;
+    if (!pinned && nblocks <= kSmallCallBlocks) {
+      // a small call: the tables come from global memory, no shared-memory fill per CTA
+      const KeyWords kw = dir == AES_ENCRYPT ? enc_key_words(*ks, iv) : dec_key_words(*ks, iv);
+      return launch_small(dir, ks->nr, kw, d_in, d_out, nblocks, st);
+    }
+  }
   if (impl == AES_IMPL_BITSLICE) return launch_bitslice(dir, *ks, iv, d_in, d_out, nblocks, st, BSConfig{});
   const KeyWords kw = dir == AES_ENCRYPT ? enc_key_words(*ks, iv) : dec_key_words(*ks, iv);
   return launch_ttable(dir, ks->nr, kw, d_in, d_out, nblocks, st, cfg);

@@ -28,6 +28,7 @@ constexpr int kDevices = 64;
 
 struct Tuned {
   bool set = false;
+  bool pinned = false;  // set by aes_set_auto_choice: serves every size, small calls too
   Candidate c{};
 };
 std::mutex g_mu;
@@ -99,8 +100,9 @@ void cache_store(const char* path, const std::string& text, const std::string& s
 
 }  // namespace
 
-bool tuned_choice(int dir, int nr, int* impl, TTConfig* cfg) {
+bool tuned_choice(int dir, int nr, int* impl, TTConfig* cfg, bool* pinned) {
   int dev = 0;
+  if (pinned) *pinned = false;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return false;
   std::lock_guard<std::mutex> lk(g_mu);
   const Tuned& t = g_tuned[dev][dir == AES_DECRYPT][(nr - 10) / 2];
@@ -108,6 +110,7 @@ bool tuned_choice(int dir, int nr, int* impl, TTConfig* cfg) {
   *impl = t.c.impl;
   cfg->threads = t.c.threads;
   cfg->unroll = t.c.unroll;
+  if (pinned) *pinned = t.pinned;
   return true;
 }
 
@@ -176,6 +179,7 @@ extern "C" aes_status aes_autotune_blocks(const aes_key_schedule* ks, const void
     std::lock_guard<std::mutex> lk(g_mu);
     Tuned& t = g_tuned[dev][dir == AES_DECRYPT][(ks->nr - 10) / 2];
     t.set = true;
+    t.pinned = false;
     t.c = best;
   }
   if (impl) *impl = best.impl;
@@ -189,14 +193,20 @@ extern "C" aes_status aes_set_auto_choice(int dir, int nr, int impl, int threads
   if (dir != AES_ENCRYPT && dir != AES_DECRYPT) return set_error(AES_EINVAL, "dir must be AES_ENCRYPT or AES_DECRYPT");
   if (nr != 10 && nr != 12 && nr != 14) return set_error(AES_EINVAL, "nr must be 10, 12 or 14");
   const Candidate c{impl, threads, unroll};
-  if (!valid(c)) return set_error(AES_EINVAL, "(impl %d, %d threads, %d per thread) is not a compiled candidate", impl, threads, unroll);
+  if (impl != AES_IMPL_AUTO && !valid(c))
+    return set_error(AES_EINVAL, "(impl %d, %d threads, %d per thread) is not a compiled candidate", impl, threads, unroll);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
   if (dev < 0 || dev >= kDevices) return set_error(AES_ECUDA, "device ordinal %d out of range", dev);
   std::lock_guard<std::mutex> lk(g_mu);
   Tuned& t = g_tuned[dev][dir == AES_DECRYPT][(nr - 10) / 2];
+  if (impl == AES_IMPL_AUTO) {  // back to the default: no tuned or pinned choice
+    t = Tuned{};
+    return AES_OK;
+  }
   t.set = true;
+  t.pinned = true;
   t.c = c;
   return AES_OK;
 }

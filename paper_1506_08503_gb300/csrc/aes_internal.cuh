@@ -76,8 +76,14 @@ aes_status launch_ttable(int dir, int nr, const KeyWords& kw, const void* d_in, 
 // The bitsliced kernels take the plain schedule (they run the paper's inverse-cipher order,
 // not the equivalent inverse cipher); the IV is folded into round key 0.
 // The tuned choice for AES_IMPL_AUTO on the current device (aes_autotune_blocks); false when
-// none was tuned (then the default T-table shape is used).
-bool tuned_choice(int dir, int nr, int* impl, TTConfig* cfg);
+// none was tuned (then the default T-table shape is used).  *pinned (if not null) tells whether
+// the choice was set by aes_set_auto_choice, which serves calls of every size.
+bool tuned_choice(int dir, int nr, int* impl, TTConfig* cfg, bool* pinned = nullptr);
+// AES_IMPL_AUTO calls of at most this many blocks (and no pinned choice) take the small-call
+// kernel, whose tables need no shared-memory fill (aes_small.cu).
+constexpr size_t kSmallCallBlocks = 32768;
+aes_status launch_small(int dir, int nr, const KeyWords& kw, const void* d_in, void* d_out, size_t nblocks,
+                        cudaStream_t stream);
 aes_status launch_bitslice(int dir, const aes_key_schedule& ks, const uint8_t* iv, const void* d_in,
                            void* d_out, size_t nblocks, cudaStream_t stream, const BSConfig& cfg);
 

@@ -54,4 +54,9 @@ def test_set_auto_choice_then_auto_matches(aes, cuda):
         assert torch.equal(aes.crypt(x, ks, "encrypt"), ref)
     aes.aes_set_auto_choice("encrypt", 10, "bitslice", 128, 32)
     assert torch.equal(aes.crypt(x, ks, "encrypt"), ref)
-    aes.aes_set_auto_choice("encrypt", 10, "ttable", 512, 2)
+    # a pinned choice serves small calls too; cleared, small calls take the small-call kernel
+    small = x[: 16 * 1000]
+    assert torch.equal(aes.crypt(small, ks, "encrypt"), ref[: 16 * 1000])
+    aes.aes_set_auto_choice("encrypt", 10, "auto", 0, 0)
+    assert torch.equal(aes.crypt(small, ks, "encrypt"), ref[: 16 * 1000])
+    assert torch.equal(aes.crypt(x, ks, "encrypt"), ref)

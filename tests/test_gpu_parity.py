@@ -101,6 +101,30 @@ def test_impls_agree_and_auto(aes, cuda):
     assert torch.equal(a, b) and torch.equal(a, c)
 
 
+@pytest.mark.parametrize("key_bits", [128, 192, 256])
+def test_small_call_kernel(aes, orc, cuda, key_bits):
+    """AES_IMPL_AUTO calls of up to 32768 blocks run the small-call kernel (tables read from
+    global memory, no shared-memory fill): ragged sizes up to the threshold, with and without
+    IV, both directions, against the oracle; one block past the threshold takes the other
+    kernel and agrees."""
+    import torch
+
+    for d in ("encrypt", "decrypt"):
+        aes.aes_set_auto_choice(d, {128: 10, 192: 12, 256: 14}[key_bits], "auto", 0, 0)  # no pinned choice
+    rng = np.random.default_rng(500 + key_bits)
+    key = rng.integers(0, 256, key_bits // 8, dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes(), key_bits)
+    for n in (1, 2, 31, 127, 129, 4096, 4097, 32768, 32769):
+        for iv in (None, rng.integers(0, 256, 16, dtype=np.uint8)):
+            data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
+            x = to_dev(data)
+            ivb = None if iv is None else iv.tobytes()
+            ct = to_host(aes.encrypt(x, ks, iv=ivb))
+            assert (ct == orc.encrypt_blocks(key, data, iv=iv, threads=THREADS)).all(), n
+            dd = to_host(aes.decrypt(x, ks, iv=ivb))
+            assert (dd == orc.decrypt_blocks(key, data, iv=iv, threads=THREADS)).all(), n
+
+
 def test_empty_is_noop(aes, cuda):
     import torch
 

@@ -31,19 +31,19 @@ SIZES = [1, 33, 1025, 77_825, 155_651, 237_571]
 
 @pytest.fixture
 def shape(request, aes_lib_ready):
-    """Sets the AES_IMPL_AUTO choice to one T-table shape for every direction and round count,
-    and restores the library default (512 threads x 2) afterwards."""
+    """Pins the AES_IMPL_AUTO choice to one T-table shape for every direction and round count
+    (so that small calls take it too), and clears it afterwards."""
     aes = aes_lib_ready
     t, u = request.param
 
-    def put(tt, uu):
+    def put(impl, tt, uu):
         for d in ("encrypt", "decrypt"):
             for nr in (10, 12, 14):
-                aes.aes_set_auto_choice(d, nr, "ttable", tt, uu)
+                aes.aes_set_auto_choice(d, nr, impl, tt, uu)
 
-    put(t, u)
+    put("ttable", t, u)
     yield t, u
-    put(512, 2)
+    put("auto", 0, 0)
 
 
 @functools.lru_cache(maxsize=None)
@@ -128,4 +128,4 @@ def test_whole_1gib_buffer(aes_lib_ready, gib, impl):
         torch.cuda.empty_cache()
     finally:
         for d in ("encrypt", "decrypt"):
-            aes.aes_set_auto_choice(d, 10, "ttable", 512, 2)
+            aes.aes_set_auto_choice(d, 10, "auto", 0, 0)
