@@ -148,6 +148,20 @@ TTDualFn ttable_batched_dual_r10(int threads, int blocks_per_lane, int nre, int 
 struct aes_batch;
 
 namespace aesgb {
+// A handful of messages launched with their descriptors as kernel parameters (no upload, no
+// graph, no shared-memory tables): the request server's path for small batches (aes_small.cu).
+constexpr int kSmallBatchMax = 16;
+struct SmallMsg {
+  uint64_t src, dst;  // byte addresses, 16-byte aligned
+  uint32_t nblocks, key_idx, dir, pad;
+};
+struct SmallBatch {
+  uint32_t n, pad;
+  uint64_t start[kSmallBatchMax + 1];  // first block of each message in the batch's block space
+  SmallMsg m[kSmallBatchMax];
+};
+aes_status launch_small_batch(const SmallBatch& b, const PoolEntry* pool, cudaStream_t stream);
+
 // Work of a direction in round-blocks: sum of nblocks x rounds[key_idx] over its messages.
 uint64_t work_of(const BatchMsg* m, size_t n, const int8_t* rounds);
 // Cuts a direction's block space (n messages, start[0..n]) into nw slices of equal work W in

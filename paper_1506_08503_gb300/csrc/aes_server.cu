@@ -219,6 +219,8 @@ void retire(aes_server* s, StreamSlot& sl, double t, int state) {
   s->cv_work.notify_one();
 }
 
+aes_status issue_batched(aes_server* s, StreamSlot& sl, cudaStream_t st, size_t nenc, size_t ndec);
+
 // Issues the tickets [sl.first, sl.last) on slot i (mu NOT held; the batch owns its ring
 // slots until the worker sees its done event and retires them).
 aes_status issue(aes_server* s, int i) {
@@ -228,6 +230,7 @@ aes_status issue(aes_server* s, int i) {
   if (sl.inject_fail) return set_error(AES_ECUDA, "injected launch failure (fail_every = %u)", s->cfg.fail_every);
   // pass 1: host payloads go to the device, and the batch is counted per direction
   size_t nenc = 0, ndec = 0;
+  uint64_t nblocks = 0;
   for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
     const Req& q = s->at(tk);
     const aes_request& r = q.r;
@@ -236,10 +239,50 @@ aes_status issue(aes_server* s, int i) {
       if ((e = cudaMemcpyAsync(to, r.src, r.length, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_error(e, "H2D");
     }
     (r.dir == AES_ENCRYPT ? nenc : ndec)++;
+    nblocks += r.length / 16;
   }
   // pass 2 (inside the batch launch): descriptors written straight into the pinned staging.
   // A device destination is the output; a host destination is served from the staging slot,
   // which also holds the input when the source was on the host.
+  const uint64_t nreq = sl.last - sl.first;
+  if (nreq <= uint64_t(kSmallBatchMax) && nblocks <= kSmallCallBlocks) {
+    // a small batch (the common case at low request rates): its descriptors travel as kernel
+    // parameters and its tables come from global memory, so it costs one kernel launch: no
+    // descriptor upload, no copy-stream event, no graph update, no shared-memory table fill
+    SmallBatch b{};
+    uint64_t pos = 0;
+    for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
+      const Req& q = s->at(tk);
+      const aes_request& r = q.r;
+      const uint64_t stage = reinterpret_cast<uint64_t>(s->arena_base + q.stage_off);
+      const uint64_t out_addr = dst_direct(s, r) ? reinterpret_cast<uint64_t>(r.dst) : stage;
+      const uint64_t in_addr = src_direct(s, r) ? reinterpret_cast<uint64_t>(r.src)
+                               : r.dst_on_device ? reinterpret_cast<uint64_t>(r.dst) : stage;
+      SmallMsg& m = b.m[b.n];
+      m = SmallMsg{in_addr, out_addr, uint32_t(r.length / 16), r.key_idx, r.dir, 0u};
+      b.start[b.n++] = pos;
+      pos += r.length / 16;
+    }
+    b.start[b.n] = pos;
+    aes_status rc = launch_small_batch(b, s->pool->entries, st);
+    if (rc != AES_OK) return rc;
+  } else {
+    aes_status rc = issue_batched(s, sl, st, nenc, ndec);
+    if (rc != AES_OK) return rc;
+  }
+  for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
+    const Req& q = s->at(tk);
+    if (!dst_direct(s, q.r))
+      if ((e = cudaMemcpyAsync(q.r.dst, s->arena_base + q.stage_off, q.r.length, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_error(e, "D2H");
+  }
+  if ((e = cudaEventRecord(sl.done_ev, st)) != cudaSuccess) return cuda_error(e, "cudaEventRecord(batch done)");
+  return AES_OK;
+}
+
+// The batched launch of a larger batch: descriptors into the pinned staging, then the cached
+// graph (batch_launch_descs).
+aes_status issue_batched(aes_server* s, StreamSlot& sl, cudaStream_t st, size_t nenc, size_t ndec) {
   auto fill = [&](BatchMsg* em, BatchMsg* dm, uint4*, uint4*) {
     size_t ie = 0, id = 0;
     for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
@@ -254,16 +297,7 @@ aes_status issue(aes_server* s, int i) {
       else dm[id++] = d;
     }
   };
-  aes_status rc = batch_launch_descs(sl.batch, nenc, ndec, fill, false, 0, 0, st);
-  if (rc != AES_OK) return rc;
-  for (uint64_t tk = sl.first; tk < sl.last; ++tk) {
-    const Req& q = s->at(tk);
-    if (!dst_direct(s, q.r))
-      if ((e = cudaMemcpyAsync(q.r.dst, s->arena_base + q.stage_off, q.r.length, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        return cuda_error(e, "D2H");
-  }
-  if ((e = cudaEventRecord(sl.done_ev, st)) != cudaSuccess) return cuda_error(e, "cudaEventRecord(batch done)");
-  return AES_OK;
+  return batch_launch_descs(sl.batch, nenc, ndec, fill, false, 0, 0, st);
 }
 
 // A slot's batch has been issued: the worker polls its done event from now on.  Called with

@@ -109,6 +109,47 @@ __global__ void __launch_bounds__(kSmallThreads) tt_small_kernel(const uint4* in
   }
 }
 
+// One block with the round keys read from a pool entry (rows in round order, nr of them
+// after the first; the same words the batched kernel keeps in registers), the tables from
+// global memory.
+template <int DIR>
+__device__ __forceinline__ uint4 crypt_pool_rows(uint4 v, const uint4* kp, int nr) {
+  uint4 k = __ldg(kp);
+  uint32_t s0 = v.x ^ k.x, s1 = v.y ^ k.y, s2 = v.z ^ k.z, s3 = v.w ^ k.w;
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    k = __ldg(kp + r);
+    g_round<DIR>(s0, s1, s2, s3, k.x, k.y, k.z, k.w);
+  }
+  for (int r = 10; r < nr; ++r) {  // AES-192 and AES-256: two or four more rounds
+    k = __ldg(kp + r);
+    g_round<DIR>(s0, s1, s2, s3, k.x, k.y, k.z, k.w);
+  }
+  k = __ldg(kp + nr);
+  return g_final<DIR>(s0, s1, s2, s3, k.x, k.y, k.z, k.w);
+}
+
+// Every block of the batch's messages (at most kSmallBatchMax, both directions, any key size)
+// in one grid-stride loop: a thread finds its block's message by a scan of the starts in the
+// constant bank.
+__global__ void __launch_bounds__(kSmallThreads) small_batch_kernel(const __grid_constant__ SmallBatch b,
+                                                                     const PoolEntry* pool) {
+  const uint64_t total = b.start[b.n];
+  const uint64_t stride = uint64_t(gridDim.x) * kSmallThreads;
+  for (uint64_t g = uint64_t(blockIdx.x) * kSmallThreads + threadIdx.x; g < total; g += stride) {
+    uint32_t m = 0;
+    while (g >= b.start[m + 1]) ++m;
+    const SmallMsg& d = b.m[m];
+    const uint64_t j = g - b.start[m];
+    const PoolEntry* e = pool + d.key_idx;
+    const int nr = __ldg(&e->nr);
+    const uint4 v = tt::ld_block(reinterpret_cast<const uint4*>(d.src) + j);
+    const uint4 o = d.dir == AES_ENCRYPT ? crypt_pool_rows<AES_ENCRYPT>(v, reinterpret_cast<const uint4*>(e->enc), nr)
+                                         : crypt_pool_rows<AES_DECRYPT>(v, reinterpret_cast<const uint4*>(e->dec), nr);
+    tt::st_block(reinterpret_cast<uint4*>(d.dst) + j, o);
+  }
+}
+
 using SmallFn = void (*)(const uint4*, uint4*, size_t, const KeyWords);
 
 SmallFn pick_small(int dir, int nr) {
@@ -133,6 +174,20 @@ aes_status launch_small(int dir, int nr, const KeyWords& kw, const void* d_in, v
                                                          nblocks, kw);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "small-call kernel launch");
+  return AES_OK;
+}
+
+aes_status launch_small_batch(const SmallBatch& b, const PoolEntry* pool, cudaStream_t stream) {
+  if (b.n == 0 || b.n > uint32_t(kSmallBatchMax)) return set_error(AES_EINVAL, "small batch of %u messages", b.n);
+  const DeviceInfo* di = current_device_info();
+  if (!di) return AES_ECUDA;
+  const uint64_t total = b.start[b.n];
+  if (total == 0) return AES_OK;
+  const uint64_t want = (total + kSmallThreads - 1) / kSmallThreads;
+  const uint64_t cap = uint64_t(di->sms) * 16;
+  small_batch_kernel<<<unsigned(want < cap ? want : cap), kSmallThreads, 0, stream>>>(b, pool);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "small-batch kernel launch");
   return AES_OK;
 }
 

@@ -269,3 +269,44 @@ def test_trickled_requests_all_complete_without_a_lost_wakeup(aes_lib_ready, orc
     for i in rng.choice(n, 60, replace=False):
         o, L = int(offs[i]), int(lengths[i])
         assert (got[o:o + L] == oracle_crypt(orc, keys[int(kidx[i])], data[o:o + L], int(dirs[i]))).all(), i
+
+
+def test_small_batches_take_the_one_launch_path(aes_lib_ready, orc):
+    """Batches of at most 16 requests and 32768 blocks run as one kernel with their descriptors
+    as launch parameters and the tables read from global memory: AES-128/192/256 keys, both
+    directions, device and host payloads in one batch, against the oracle; a batch just over
+    the limit takes the batched graph path and gives the same bytes."""
+    import torch
+
+    rng = np.random.default_rng(49)
+    bits = [128, 192, 256, 128, 256, 192]
+    keys = [rng.integers(0, 256, b // 8, dtype=np.uint8) for b in bits]
+    pool = aes.KeyPool(len(keys))
+    for i, k in enumerate(keys):
+        pool.set(i, aes.aes_key_expand(k.tobytes(), 8 * len(k)))
+    with pool, aes.Server(pool, hbm_budget=64 << 20, nstreams=2, max_batch=64) as srv:
+        for count, max_blocks in ((10, 300), (16, 2048), (17, 100), (3, 12000)):
+            lengths = rng.integers(1, max_blocks, count) * 16
+            offs = np.concatenate([[0], np.cumsum(lengths)[:-1]]).astype(np.int64)
+            data = rng.integers(0, 256, int(lengths.sum()), dtype=np.uint8)
+            src = torch.from_numpy(data).cuda()
+            dst = torch.zeros_like(src)
+            hdst = np.zeros_like(data)
+            torch.cuda.synchronize()
+            reqs = np.zeros(count, dtype=aes.request_dtype())
+            reqs["key_idx"] = rng.integers(0, len(keys), count)
+            reqs["dir"] = rng.integers(0, 2, count)
+            reqs["length"] = lengths
+            reqs["src"] = src.data_ptr() + offs
+            on_host = np.arange(count) % 3 == 2  # every third output goes to host memory
+            reqs["dst"] = np.where(on_host, hdst.ctypes.data + offs, dst.data_ptr() + offs)
+            reqs["src_on_device"] = 1
+            reqs["dst_on_device"] = np.where(on_host, 0, 1)
+            tickets = srv.submit_many(reqs)
+            assert all(srv.poll(int(t)) == aes.AES_REQ_DONE for t in tickets)
+            got_dev = dst.cpu().numpy()
+            for i in range(count):
+                o, L = int(offs[i]), int(lengths[i])
+                got = hdst[o:o + L] if on_host[i] else got_dev[o:o + L]
+                want = oracle_crypt(orc, keys[int(reqs[i]["key_idx"])], data[o:o + L], int(reqs[i]["dir"]))
+                assert (got == want).all(), (count, i)
