@@ -55,6 +55,55 @@ cbc_encrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride,
   }
 }
 
+// Few messages: the chain's latency is the bound, and one lane per chain spends it issuing a
+// whole block's round (16 byte permutes, 16 lookups, 8 three-input XORs on one scheduler)
+// before the next round can start.  Here four lanes share a chain, lane q holding column q of
+// the state: a round is three shuffles (the other columns), four lookups and two XORs per
+// lane, the same output column as tt_round computes for column q.  Each lane keeps its column
+// of every round key in registers; the four lanes of a chain load and store one 16-byte block
+// together.
+template <int NR>
+__device__ __forceinline__ uint32_t col_shfl(uint32_t s, uint32_t lane, uint32_t d) {
+  return __shfl_sync(0xFu << (lane & ~3u), s, (lane & ~3u) | ((lane + d) & 3u));
+}
+
+constexpr unsigned kColThreads = 128;
+constexpr uint64_t kColChainsPerSm = 64;  // up to 8 warps of four-lane chains per SM
+
+template <int NR>
+__global__ void __launch_bounds__(kColThreads, 1)
+cbc_encrypt_cols(const uint4* in, uint4* out, const uint4* ivs, int iv_stride, uint64_t nmsgs, uint64_t mblocks,
+                 const KeyWords kw) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  fill_tables<AES_ENCRYPT>(smem);
+  __syncthreads();
+  const char* sm = reinterpret_cast<const char*>(smem);
+  const uint32_t lane = threadIdx.x & 31u, q = lane & 3u;
+  const uint32_t lc = lane * 4u;
+  uint32_t kq[NR + 1];
+#pragma unroll
+  for (int r = 0; r <= NR; ++r) kq[r] = kw.w[r][q];
+  const uint64_t groups = (uint64_t(gridDim.x) * kColThreads) >> 2;
+  for (uint64_t msg = (uint64_t(blockIdx.x) * kColThreads + threadIdx.x) >> 2; msg < nmsgs; msg += groups) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(in + msg * mblocks) + q;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out + msg * mblocks) + q;
+    uint32_t chain = reinterpret_cast<const uint32_t*>(ivs + (iv_stride ? msg : 0))[q];
+    uint32_t next = src[0];  // coherent loads: encryption may run in place
+    for (uint64_t j = 0; j < mblocks; ++j) {
+      uint32_t s = next ^ chain ^ kq[0];
+      if (j + 1 < mblocks) next = src[4 * (j + 1)];
+#pragma unroll
+      for (int r = 1; r < NR; ++r) {
+        const uint32_t s1 = col_shfl<NR>(s, lane, 1), s2 = col_shfl<NR>(s, lane, 2), s3 = col_shfl<NR>(s, lane, 3);
+        s = tt::tt<0, 0>(sm, s, lc) ^ tt::tt<1, 1>(sm, s1, lc) ^ tt::tt<2, 2>(sm, s2, lc) ^ tt::tt<3, 3>(sm, s3, lc) ^ kq[r];
+      }
+      const uint32_t s1 = col_shfl<NR>(s, lane, 1), s2 = col_shfl<NR>(s, lane, 2), s3 = col_shfl<NR>(s, lane, 3);
+      chain = pick_bytes(tt::tt<2, 0>(sm, s, lc), tt::tt<3, 1>(sm, s1, lc), tt::tt<0, 2>(sm, s2, lc), tt::tt<1, 3>(sm, s3, lc)) ^ kq[NR];
+      dst[4 * j] = chain;
+    }
+  }
+}
+
 // Many messages: each warp owns kRows = 32 consecutive messages (one chain per lane) and
 // moves them through shared memory kStage blocks at a time, so that global loads and stores
 // are coalesced (a warp instruction covers 4 rows x 128 contiguous bytes instead of 32
@@ -204,6 +253,10 @@ CbcKernel pick_staged(int nr, unsigned threads) {
   return threads == 512 ? pick_staged_nr<512>(nr) : threads == 576 ? pick_staged_nr<576>(nr) : pick_staged_nr<640>(nr);
 }
 
+CbcKernel pick_cols(int nr) {
+  return nr == 10 ? cbc_encrypt_cols<10> : nr == 12 ? cbc_encrypt_cols<12> : cbc_encrypt_cols<14>;
+}
+
 CbcKernel pick_encrypt(int nr) {
   return nr == 10 ? cbc_encrypt_kernel<10> : nr == 12 ? cbc_encrypt_kernel<12> : cbc_encrypt_kernel<14>;
 }
@@ -242,7 +295,12 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   // staged kernel; fewer messages are latency-bound chains, better spread one per lane
   const bool staged = dir == AES_ENCRYPT && nmsgs >= uint64_t(di->sms) * kStagedThreads;
   const unsigned staged_cta = staged ? staged_threads((nmsgs + kRows - 1) / kRows, di->sms) : 0u;
-  CbcKernel k = dir == AES_DECRYPT ? nullptr : staged ? pick_staged(ks->nr, staged_cta) : pick_encrypt(ks->nr);
+  // few chains: four lanes per chain (up to 8 warps' worth of chains per SM)
+  const bool cols = dir == AES_ENCRYPT && !staged && nmsgs <= uint64_t(di->sms) * kColChainsPerSm;
+  CbcKernel k = dir == AES_DECRYPT ? nullptr
+                : staged           ? pick_staged(ks->nr, staged_cta)
+                : cols             ? pick_cols(ks->nr)
+                                   : pick_encrypt(ks->nr);
   CbcDecKernel kd = dir == AES_DECRYPT ? pick_decrypt(ks->nr) : nullptr;
   const size_t smem = ttable_smem_bytes(dir) + (staged ? size_t(staged_cta / 32) * kTileBytes : 0);
   aes_status ast = ensure_kernel_smem(k ? reinterpret_cast<const void*>(k) : reinterpret_cast<const void*>(kd), smem);
@@ -253,6 +311,9 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   if (staged) {
     threads = staged_cta;  // the kernel instance's warp-to-group map assumes this CTA size
     work = (nmsgs + kRows - 1) / kRows * 32;  // kRows messages per warp
+  } else if (cols) {
+    threads = kColThreads;
+    work = nmsgs * 4;  // four lanes per chain
   } else if (dir == AES_ENCRYPT) {
     // a lane per message: with few messages, spread the chains over all SMs (smaller CTAs)
     // rather than packing them into a few
