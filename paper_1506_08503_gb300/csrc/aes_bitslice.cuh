@@ -50,6 +50,33 @@ struct Masks {
   uint32_t m[kBsMaxRounds + 1][128];
 };
 
+// (a & M) | (b & ~M) for a constant mask M.  On the device one LOP3 with M as its immediate:
+// written in C, the compiler moved the mask across the transposes' shifts and spent two
+// instructions per output.
+template <uint32_t M>
+BS_FN uint32_t select_bits(uint32_t a, uint32_t b) {
+#if defined(__CUDA_ARCH__)
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(d) : "r"(a), "r"(b), "n"(M));
+  return d;
+#else
+  return (a & M) | (b & ~M);
+#endif
+}
+
+// One shift stage of the transpose: swaps the J-bit sub-blocks between rows k and k + J.
+template <int J>
+BS_FN void swap_stage(uint32_t* a) {
+  constexpr uint32_t m = J == 4 ? 0x0F0F0F0Fu : J == 2 ? 0x33333333u : 0x55555555u;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k & J) continue;
+    const uint32_t x = a[k], y = a[k + J];
+    a[k] = select_bits<m>(x, y << J);
+    a[k + J] = select_bits<m>(x >> J, y);
+  }
+}
+
 // 32x32 bit transpose in place: afterwards bit j of a[p] is the old bit p of a[j].
 BS_FN void transpose32(uint32_t* a) {
 #pragma unroll
@@ -65,17 +92,9 @@ BS_FN void transpose32(uint32_t* a) {
     a[k] = byte_perm(x, y, 0x6240u);
     a[k + 8] = byte_perm(x, y, 0x7351u);
   }
-#pragma unroll
-  for (int j = 4; j >= 1; j >>= 1) {
-    const uint32_t m = j == 4 ? 0x0F0F0F0Fu : j == 2 ? 0x33333333u : 0x55555555u;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      if (k & j) continue;
-      const uint32_t x = a[k], y = a[k + j];
-      a[k] = (x & m) | ((y << j) & ~m);
-      a[k + j] = (y & ~m) | ((x >> j) & m);
-    }
-  }
+  swap_stage<4>(a);
+  swap_stage<2>(a);
+  swap_stage<1>(a);
 }
 
 BS_FN uint32_t xor3(uint32_t a, uint32_t b, uint32_t c) { return a ^ b ^ c; }
