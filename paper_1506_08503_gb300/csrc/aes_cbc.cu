@@ -13,6 +13,8 @@
 // Decryption has no chain: every block needs only its own ciphertext and the previous one, so
 // it runs one block per lane over the whole matrix like the independent-block kernel, with
 // one extra (mostly L1-hit) load of the previous block.  It cannot run in place.
+#include <algorithm>
+
 #include "aes_ttable.cuh"
 
 namespace aesgb {
@@ -55,51 +57,49 @@ cbc_encrypt_kernel(const uint4* in, uint4* out, const uint4* ivs, int iv_stride,
   }
 }
 
-// Few messages: the chain's latency is the bound, and one lane per chain spends it issuing a
-// whole block's round (16 byte permutes, 16 lookups, 8 three-input XORs on one scheduler)
-// before the next round can start.  Here four lanes share a chain, lane q holding column q of
-// the state: a round is three shuffles (the other columns), four lookups and two XORs per
-// lane, the same output column as tt_round computes for column q.  Each lane keeps its column
-// of every round key in registers; the four lanes of a chain load and store one 16-byte block
-// together.
-template <int NR>
-__device__ __forceinline__ uint32_t col_shfl(uint32_t s, uint32_t lane, uint32_t d) {
-  return __shfl_sync(0xFu << (lane & ~3u), s, (lane & ~3u) | ((lane + d) & 3u));
-}
-
-constexpr unsigned kColThreads = 128;
-constexpr uint64_t kColChainsPerSm = 64;  // up to 8 warps of four-lane chains per SM
+// Few messages: the chain's latency is the bound.  One lane per chain spends it issuing a
+// whole block's round (16 byte permutes and lookups) before the next round can start; here
+// four lanes share a chain, lane q holding column q of the state (col_round: four lookups,
+// three shuffles, two XORs per lane and round).  A warp runs `cpw` chains (lanes 4 cpw.. idle)
+// and the first `wpc` warps of a CTA run chains (all of them fill the tables): with few chains
+// one per warp, since every chain a warp adds makes each of its shuffles and lookups slower;
+// with many, up to eight per warp, since the SM's shared-memory pipe is then the bound.  Each
+// lane keeps its column of every round key in registers; the four lanes of a chain load and
+// store one 16-byte block together.  The next block's plaintext, the first round key and the
+// last one are combined off the chain's dependent path.
+constexpr unsigned kColMaxThreads = 256;
+constexpr uint64_t kColChainsPerSm = 64;  // up to 8 warps of 8 chains per SM
 
 template <int NR>
-__global__ void __launch_bounds__(kColThreads, 1)
+__global__ void __launch_bounds__(kColMaxThreads, 1)
 cbc_encrypt_cols(const uint4* in, uint4* out, const uint4* ivs, int iv_stride, uint64_t nmsgs, uint64_t mblocks,
-                 const KeyWords kw) {
+                 const KeyWords kw, uint32_t cpw, uint32_t wpc) {
   extern __shared__ __align__(16) uint32_t smem[];
   fill_tables<AES_ENCRYPT>(smem);
   __syncthreads();
   const char* sm = reinterpret_cast<const char*>(smem);
-  const uint32_t lane = threadIdx.x & 31u, q = lane & 3u;
+  const uint32_t lane = threadIdx.x & 31u, q = lane & 3u, slot = lane >> 2;
   const uint32_t lc = lane * 4u;
+  if (slot >= cpw || (threadIdx.x >> 5) >= wpc) return;
   uint32_t kq[NR + 1];
 #pragma unroll
   for (int r = 0; r <= NR; ++r) kq[r] = kw.w[r][q];
-  const uint64_t groups = (uint64_t(gridDim.x) * kColThreads) >> 2;
-  for (uint64_t msg = (uint64_t(blockIdx.x) * kColThreads + threadIdx.x) >> 2; msg < nmsgs; msg += groups) {
+  const uint32_t k_last_first = kq[NR] ^ kq[0];
+  // warp w of CTA b is global warp w * grid + b: consecutive chains go to different SMs first
+  const uint64_t warp = uint64_t(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const uint64_t step = uint64_t(gridDim.x) * wpc * cpw;
+  for (uint64_t msg = warp * cpw + slot; msg < nmsgs; msg += step) {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(in + msg * mblocks) + q;
     uint32_t* dst = reinterpret_cast<uint32_t*>(out + msg * mblocks) + q;
-    uint32_t chain = reinterpret_cast<const uint32_t*>(ivs + (iv_stride ? msg : 0))[q];
-    uint32_t next = src[0];  // coherent loads: encryption may run in place
+    // coherent loads: encryption may run in place
+    uint32_t s = src[0] ^ reinterpret_cast<const uint32_t*>(ivs + (iv_stride ? msg : 0))[q] ^ kq[0];
     for (uint64_t j = 0; j < mblocks; ++j) {
-      uint32_t s = next ^ chain ^ kq[0];
-      if (j + 1 < mblocks) next = src[4 * (j + 1)];
+      const uint32_t next = j + 1 < mblocks ? src[4 * (j + 1)] : 0u;
 #pragma unroll
-      for (int r = 1; r < NR; ++r) {
-        const uint32_t s1 = col_shfl<NR>(s, lane, 1), s2 = col_shfl<NR>(s, lane, 2), s3 = col_shfl<NR>(s, lane, 3);
-        s = tt::tt<0, 0>(sm, s, lc) ^ tt::tt<1, 1>(sm, s1, lc) ^ tt::tt<2, 2>(sm, s2, lc) ^ tt::tt<3, 3>(sm, s3, lc) ^ kq[r];
-      }
-      const uint32_t s1 = col_shfl<NR>(s, lane, 1), s2 = col_shfl<NR>(s, lane, 2), s3 = col_shfl<NR>(s, lane, 3);
-      chain = pick_bytes(tt::tt<2, 0>(sm, s, lc), tt::tt<3, 1>(sm, s1, lc), tt::tt<0, 2>(sm, s2, lc), tt::tt<1, 3>(sm, s3, lc)) ^ kq[NR];
-      dst[4 * j] = chain;
+      for (int r = 1; r < NR; ++r) s = col_round(s, kq[r], sm, lane, lc);
+      const uint32_t p = col_last(s, sm, lane, lc);
+      dst[4 * j] = p ^ kq[NR];
+      s = p ^ (next ^ k_last_first);  // C_j ^ P_j+1 ^ K_0
     }
   }
 }
@@ -253,7 +253,10 @@ CbcKernel pick_staged(int nr, unsigned threads) {
   return threads == 512 ? pick_staged_nr<512>(nr) : threads == 576 ? pick_staged_nr<576>(nr) : pick_staged_nr<640>(nr);
 }
 
-CbcKernel pick_cols(int nr) {
+using CbcColsKernel = void (*)(const uint4*, uint4*, const uint4*, int, uint64_t, uint64_t, const KeyWords, uint32_t,
+                              uint32_t);
+
+CbcColsKernel pick_cols(int nr) {
   return nr == 10 ? cbc_encrypt_cols<10> : nr == 12 ? cbc_encrypt_cols<12> : cbc_encrypt_cols<14>;
 }
 
@@ -266,6 +269,25 @@ CbcDecKernel pick_decrypt(int nr) {
 }
 
 }  // namespace
+
+ColsShape cols_shape(uint64_t chains, int sms) {
+  const uint64_t per_sm = (chains + uint64_t(sms) - 1) / uint64_t(sms);
+  unsigned warps, cpw;
+  if (per_sm <= 4) {  // latency-bound: one chain per warp, at most one warp per scheduler
+    cpw = 1;
+    warps = unsigned(per_sm);
+  } else if (per_sm <= 32) {  // four warps, the chains shared out among them
+    warps = 4;
+    cpw = unsigned((per_sm + 3) / 4);
+  } else {  // the shared-memory pipe is the bound: eight chains per warp
+    cpw = 8;
+    warps = unsigned(std::min<uint64_t>(kColMaxThreads / 32, (per_sm + 7) / 8));
+  }
+  const uint64_t per_cta = uint64_t(warps) * cpw;
+  const uint64_t want = (chains + per_cta - 1) / per_cta;
+  return ColsShape{std::max(128u, 32u * warps), warps, unsigned(std::min<uint64_t>(want, uint64_t(sms))), cpw};
+}
+
 }  // namespace aesgb
 
 using namespace aesgb;
@@ -295,25 +317,33 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   // staged kernel; fewer messages are latency-bound chains, better spread one per lane
   const bool staged = dir == AES_ENCRYPT && nmsgs >= uint64_t(di->sms) * kStagedThreads;
   const unsigned staged_cta = staged ? staged_threads((nmsgs + kRows - 1) / kRows, di->sms) : 0u;
-  // few chains: four lanes per chain (up to 8 warps' worth of chains per SM)
-  const bool cols = dir == AES_ENCRYPT && !staged && nmsgs <= uint64_t(di->sms) * kColChainsPerSm;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e;
+  // few chains: four lanes per chain
+  if (dir == AES_ENCRYPT && !staged && nmsgs <= uint64_t(di->sms) * kColChainsPerSm) {
+    const CbcColsKernel kc = pick_cols(ks->nr);
+    const size_t smem = ttable_smem_bytes(dir);
+    aes_status ast = ensure_kernel_smem(reinterpret_cast<const void*>(kc), smem);
+    if (ast != AES_OK) return ast;
+    const ColsShape sh = cols_shape(nmsgs, di->sms);
+    kc<<<sh.grid, sh.threads, smem, st>>>(static_cast<const uint4*>(d_in), static_cast<uint4*>(d_out),
+                                          static_cast<const uint4*>(d_ivs), iv_per_msg, nmsgs, blocks_per_msg, kw, sh.cpw,
+                                          sh.wpc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "CBC kernel launch");
+    return AES_OK;
+  }
   CbcKernel k = dir == AES_DECRYPT ? nullptr
                 : staged           ? pick_staged(ks->nr, staged_cta)
-                : cols             ? pick_cols(ks->nr)
                                    : pick_encrypt(ks->nr);
   CbcDecKernel kd = dir == AES_DECRYPT ? pick_decrypt(ks->nr) : nullptr;
   const size_t smem = ttable_smem_bytes(dir) + (staged ? size_t(staged_cta / 32) * kTileBytes : 0);
   aes_status ast = ensure_kernel_smem(k ? reinterpret_cast<const void*>(k) : reinterpret_cast<const void*>(kd), smem);
   if (ast != AES_OK) return ast;
-  cudaError_t e;
   unsigned threads = dir == AES_DECRYPT ? kDecThreads : 512u;
   uint64_t work = uint64_t(nmsgs) * blocks_per_msg;
   if (staged) {
     threads = staged_cta;  // the kernel instance's warp-to-group map assumes this CTA size
     work = (nmsgs + kRows - 1) / kRows * 32;  // kRows messages per warp
-  } else if (cols) {
-    threads = kColThreads;
-    work = nmsgs * 4;  // four lanes per chain
   } else if (dir == AES_ENCRYPT) {
     // a lane per message: with few messages, spread the chains over all SMs (smaller CTAs)
     // rather than packing them into a few
@@ -323,7 +353,6 @@ extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_iv
   }
   const uint64_t want = (work + threads - 1) / threads;
   const unsigned grid = unsigned(want < uint64_t(di->sms) ? want : uint64_t(di->sms));
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (kd) {
     const uint64_t stride = uint64_t(grid) * threads;
     kd<<<grid, threads, smem, st>>>(static_cast<const uint4*>(d_in), static_cast<uint4*>(d_out),

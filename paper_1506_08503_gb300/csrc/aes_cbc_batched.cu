@@ -3,11 +3,12 @@
 // matrix V): C_j = E_Ki(P_j ^ C_{j-1}), C_{-1} = IV_i (App. A1), and P_j = D_Ki(C_j) ^ C_{j-1}
 // (App. A4).
 //
-// Encryption is a chain inside each message, so it runs one lane per message: the host sorts
-// the messages by length (longest first), so that the lanes of a warp finish together, and
-// each lane keeps its message's round keys in registers (AES-128/192/256 mixed: the round
-// count is read with the key).  Its rate is the chain's latency, one block per ten or fourteen
-// dependent rounds per message, as for aes_cbc_crypt with few messages.
+// Encryption is a chain inside each message.  Up to 64 messages per SM run four lanes to a
+// message (a lane per state column, as aes_cbc_crypt does with few messages), more run one
+// lane per message; the host sorts the messages by length (longest first), so that the chains
+// sharing a warp finish together, and the round keys stay in registers (AES-128/192/256
+// mixed: the round count is read with the key).  Its rate is the chain's latency, one block
+// per ten to fourteen dependent rounds per message.
 //
 // Decryption has no chain: it is the batched kernel (messages laid end to end, warp slices of
 // equal work in blocks x rounds) with each block's output XORed with the previous ciphertext
@@ -57,6 +58,57 @@ cbc_enc_msgs(uint64_t in_base, uint64_t out_base, const CbcMsg* msgs, uint32_t n
       if (j + 1 < nb) next = __ldg(src + j + 1);
       chain = crypt_rt<AES_ENCRYPT>(xor4(p, chain), kw, kl, nr, sm, lc);
       st_block(dst + j, chain);
+    }
+  }
+}
+
+// Few messages: four lanes per message (tt::col_round), lane q holding column q of the state
+// and of every round key, `cpw` messages per warp in the first `wpc` warps of each CTA (see
+// cols_shape); consecutive messages (the longest first) go to different SMs first.
+constexpr int kColMaxThreads = 256;
+constexpr uint64_t kColChainsPerSm = 64;
+
+__global__ void __launch_bounds__(kColMaxThreads, 1)
+cbc_enc_msgs_cols(uint64_t in_base, uint64_t out_base, const CbcMsg* msgs, uint32_t n, const PoolEntry* pool,
+                  uint32_t cpw, uint32_t wpc) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  fill_tables<AES_ENCRYPT>(smem);
+  __syncthreads();
+  const char* sm = reinterpret_cast<const char*>(smem);
+  const uint32_t lane = threadIdx.x & 31u, q = lane & 3u, slot = lane >> 2;
+  const uint32_t lc = lane * 4u;
+  if (slot >= cpw || (threadIdx.x >> 5) >= wpc) return;
+  const uint32_t warp = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const uint32_t step = gridDim.x * wpc * cpw;
+  for (uint32_t m = warp * cpw + slot; m < n; m += step) {
+    const CbcMsg* d = msgs + m;
+    const uint64_t nb = ldg64(&d->nblocks);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(in_base + ldg64(&d->src_block) * 16u) + q;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out_base + ldg64(&d->dst_block) * 16u) + q;
+    const PoolEntry* e = pool + __ldg(&d->key_idx);
+    const int nr = __ldg(&e->nr);
+    uint32_t kq[kMaxRounds];
+#pragma unroll
+    for (int r = 0; r < kMaxRounds; ++r) kq[r] = __ldg(&e->enc[r][q]);
+    const uint32_t kl = __ldg(&e->enc[nr][q]);
+    const uint32_t k_last_first = kl ^ kq[0];
+    // coherent loads of the data: encryption may run in place
+    uint32_t s = nb ? src[0] ^ __ldg(reinterpret_cast<const uint32_t*>(&d->iv) + q) ^ kq[0] : 0u;
+    for (uint64_t j = 0; j < nb; ++j) {
+      const uint32_t next = j + 1 < nb ? src[4 * (j + 1)] : 0u;
+#pragma unroll
+      for (int r = 1; r < 10; ++r) s = col_round(s, kq[r], sm, lane, lc);
+      if (nr > 10) {  // the same in the four lanes of a message
+        s = col_round(s, kq[10], sm, lane, lc);
+        s = col_round(s, kq[11], sm, lane, lc);
+        if (nr > 12) {
+          s = col_round(s, kq[12], sm, lane, lc);
+          s = col_round(s, kq[13], sm, lane, lc);
+        }
+      }
+      const uint32_t p = col_last(s, sm, lane, lc);
+      dst[4 * j] = p ^ kl;
+      s = p ^ (next ^ k_last_first);  // C_j ^ P_j+1 ^ K_0
     }
   }
 }
@@ -203,7 +255,14 @@ extern "C" aes_status aes_cbc_batched(aes_keypool* pool, const aes_msg* msgs, co
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if ((e = cudaMemcpyAsync(c->dev, h, total, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_error(e, "descriptor upload");
   const uint64_t in_base = reinterpret_cast<uint64_t>(d_in), out_base = reinterpret_cast<uint64_t>(d_out);
-  if (!enc.empty()) {
+  if (!enc.empty() && enc.size() <= uint64_t(di->sms) * kColChainsPerSm) {
+    const size_t smem = ttable_smem_bytes(AES_ENCRYPT);
+    if ((st = ensure_kernel_smem(reinterpret_cast<const void*>(cbc_enc_msgs_cols), smem)) != AES_OK) return st;
+    const ColsShape sh = cols_shape(enc.size(), di->sms);
+    cbc_enc_msgs_cols<<<sh.grid, sh.threads, smem, s>>>(in_base, out_base, reinterpret_cast<const CbcMsg*>(c->dev + off_enc),
+                                                        uint32_t(enc.size()), pool->entries, sh.cpw, sh.wpc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "CBC encryption launch");
+  } else if (!enc.empty()) {
     const size_t smem = ttable_smem_bytes(AES_ENCRYPT);
     if ((st = ensure_kernel_smem(reinterpret_cast<const void*>(cbc_enc_msgs), smem)) != AES_OK) return st;
     // a lane per message, spread over the SMs when there are few (the chains are the bound)

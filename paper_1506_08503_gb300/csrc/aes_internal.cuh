@@ -90,6 +90,15 @@ aes_status launch_bitslice(int dir, const aes_key_schedule& ks, const uint8_t* i
 // Shared-memory bytes one T-table CTA needs for direction `dir`.
 size_t ttable_smem_bytes(int dir);
 
+// Launch shape of a four-lanes-per-chain CBC encryption (tt::col_round) over `chains` chains:
+// CTA threads (at least 128, so that the table fill is quick), the warps of a CTA that run
+// chains (the others only help fill the tables), grid, and chains per warp (lanes 4 cpw .. 31
+// of each chain warp idle).
+struct ColsShape {
+  unsigned threads, wpc, grid, cpw;
+};
+ColsShape cols_shape(uint64_t chains, int sms);
+
 // ---- key pool ------------------------------------------------------------------------------
 // One device-resident key: the encryption words and the equivalent-inverse-cipher words
 // (InvMixColumns applied to the middle round keys), both in round order.  512 bytes.

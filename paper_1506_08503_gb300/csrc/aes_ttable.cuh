@@ -143,6 +143,30 @@ __device__ __forceinline__ void st_block(uint4* p, uint4 v) {
   asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
 }
 
+// ---- four lanes per block (CBC encryption chains, where latency is the bound) ----------------
+// Lane q of an aligned group of four holds column q of the state.  Byte i of column q feeds
+// output column q - i through T_i, so each lane looks up its own four bytes at once and the
+// three words bound for other columns move to their lanes by shuffles inside the group:
+// per round one byte permute + lookup, one shuffle and two XORs on the dependent path.
+__device__ __forceinline__ uint32_t group_shfl(uint32_t v, uint32_t lane, uint32_t d) {
+  return __shfl_sync(0xFu << (lane & ~3u), v, (lane & ~3u) | ((lane + d) & 3u));
+}
+
+// One middle encryption round of column lane & 3 with its round-key word k.
+__device__ __forceinline__ uint32_t col_round(uint32_t s, uint32_t k, const char* sm, uint32_t lane, uint32_t lc) {
+  const uint32_t a1 = tt<1, 1>(sm, s, lc), a2 = tt<2, 2>(sm, s, lc), a3 = tt<3, 3>(sm, s, lc);
+  const uint32_t a0 = tt<0, 0>(sm, s, lc);
+  return a0 ^ group_shfl(a1, lane, 1) ^ group_shfl(a2, lane, 2) ^ group_shfl(a3, lane, 3) ^ k;
+}
+
+// The last encryption round before its AddRoundKey (S-box bytes picked out of the table
+// words, as in tt_final); the caller adds the last round key.
+__device__ __forceinline__ uint32_t col_last(uint32_t s, const char* sm, uint32_t lane, uint32_t lc) {
+  const uint32_t b1 = tt<3, 1>(sm, s, lc), b2 = tt<0, 2>(sm, s, lc), b3 = tt<1, 3>(sm, s, lc);
+  const uint32_t b0 = tt<2, 0>(sm, s, lc);
+  return pick_bytes(b0, group_shfl(b1, lane, 1), group_shfl(b2, lane, 2), group_shfl(b3, lane, 3));
+}
+
 template <int NR, int DIR, int THREADS, int U>
 __global__ void __launch_bounds__(THREADS, 1)
 tt_kernel(const uint4* in, uint4* out, size_t nblocks, const KeyWords kw) {

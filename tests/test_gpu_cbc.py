@@ -156,3 +156,37 @@ def test_staged_encrypt_each_cta_size(aes_lib_ready, orc, n):
     for k in range(rows.size):
         assert (c[k] == orc.cbc_encrypt(key, v, p[k])).all(), rows[k]
     assert torch.equal(aes.cbc(ct, ks, iv, "decrypt"), x)
+
+
+def _sms():
+    import torch
+
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+# message counts that reach every launch shape of the four-lanes-per-chain encryption (per SM:
+# up to 4 chains one per warp, up to 32 on four warps, up to 64 at eight chains per warp) and
+# the one-lane kernel just past it: per-SM counts times the device's SM count, plus ragged ones
+CHAINS_PER_SM = [(0, 1), (0, 129), (4, 0), (4, 1), (20, 7), (32, 0), (32, 1), (64, 0), (64, 1)]
+
+
+@pytest.mark.parametrize("per_sm,extra", CHAINS_PER_SM, ids=[f"{a}xSM+{b}" for a, b in CHAINS_PER_SM])
+def test_encrypt_chain_shapes(aes_lib_ready, orc, per_sm, extra):
+    """CBC encryption at every chains-per-warp shape: sampled messages (first, last and 150
+    random ones, each with its own IV) against the oracle, then the whole matrix round trip."""
+    import torch
+
+    n, m = per_sm * _sms() + extra, 3
+    rng = np.random.default_rng(84 + n)
+    key = rng.integers(0, 256, 32 if per_sm == 20 else 16, dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes(), 8 * key.size)
+    pt = rng.integers(0, 256, (n, 16 * m), dtype=np.uint8)
+    ivs = rng.integers(0, 256, (n, 16), dtype=np.uint8)
+    x = dev(pt)
+    ct = aes.cbc(x, ks, dev(ivs), "encrypt").cpu().numpy()
+    rows = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 150)]))
+    for i in rows:
+        assert (ct[i] == orc.cbc_encrypt(key, ivs[i], pt[i])).all(), i
+    back = aes.cbc(dev(ct), ks, dev(ivs), "decrypt")
+    torch.cuda.synchronize()
+    assert torch.equal(back, x)
