@@ -184,6 +184,80 @@ class Clocks:
 
 # ---------------------------------------------------------------------------------------------
 
+def openssl_ecb(key: np.ndarray, data: np.ndarray, cores: int, seconds: float, check: np.ndarray | None):
+    """Context, not a target: AES-128 ECB encryption of `data` through the host's OpenSSL
+    (libcrypto's EVP interface, which uses the CPU's AES instructions), the kind of CPU library
+    the paper compares against (Section IV), on `cores` threads for about `seconds`.  `check`,
+    if given, is the expected ciphertext of the first blocks.  None when no libcrypto loads."""
+    import ctypes
+    import ctypes.util
+    import threading
+
+    lib = None
+    for name in [ctypes.util.find_library("crypto"), "libcrypto.so.3", "libcrypto.so.1.1", "libcrypto.so"]:
+        if not name:
+            continue
+        try:
+            lib = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    if lib is None:
+        return None
+    vp, ip = ctypes.c_void_p, ctypes.c_int
+    lib.EVP_CIPHER_CTX_new.restype = vp
+    lib.EVP_aes_128_ecb.restype = vp
+    lib.EVP_EncryptInit_ex.argtypes = [vp, vp, vp, vp, vp]
+    lib.EVP_CIPHER_CTX_set_padding.argtypes = [vp, ip]
+    lib.EVP_EncryptUpdate.argtypes = [vp, vp, ctypes.POINTER(ip), vp, ip]
+    lib.EVP_CIPHER_CTX_free.argtypes = [vp]
+    kb = np.ascontiguousarray(key, dtype=np.uint8)
+    out = np.empty_like(data)
+    n = data.size // 16
+    bounds = [16 * (n * i // cores) for i in range(cores + 1)]
+    done = [0] * cores
+    stop = time.perf_counter() + seconds
+    errors = []
+
+    def work(i):
+        ctx = lib.EVP_CIPHER_CTX_new()
+        try:
+            if not ctx or lib.EVP_EncryptInit_ex(ctx, lib.EVP_aes_128_ecb(), None, kb.ctypes.data, None) != 1:
+                errors.append("EVP_EncryptInit_ex")
+                return
+            lib.EVP_CIPHER_CTX_set_padding(ctx, 0)
+            outl = ip(0)
+            lo, hi = bounds[i], bounds[i + 1]
+            while True:
+                for a in range(lo, hi, 1 << 26):  # 64 MiB per call
+                    b = min(hi, a + (1 << 26))
+                    if lib.EVP_EncryptUpdate(ctx, out.ctypes.data + a, ctypes.byref(outl), data.ctypes.data + a,
+                                             b - a) != 1:
+                        errors.append("EVP_EncryptUpdate")
+                        return
+                    done[i] += b - a
+                if time.perf_counter() >= stop:
+                    return
+        finally:
+            if ctx:
+                lib.EVP_CIPHER_CTX_free(ctx)
+
+    t = time.perf_counter()
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(cores)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    dt = time.perf_counter() - t
+    if errors:
+        return {"error": errors[0]}
+    res = {"encrypt_gbs": sum(done) / dt / 1e9, "threads": cores, "bytes": int(sum(done)), "seconds": dt,
+           "library": "OpenSSL libcrypto EVP aes-128-ecb", "role": "context (a CPU library comparator), not a target"}
+    if check is not None:
+        res["matches_gpu_on_first_blocks"] = bool(np.array_equal(out[: check.size], check))
+    return res
+
+
 def oracle_rate(orc, key, data_blocks: np.ndarray, cores: int, target_s: float, max_blocks: int) -> tuple[float, int]:
     """Calibrate: oracle blocks per second (encrypt) on `cores` threads."""
     probe = min(max_blocks, max(cores * 256, 4096))
@@ -936,6 +1010,7 @@ def run_ours(args):
         cpu = {"value": 2 * s * 16 / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {s} blocks of the 1 GiB seed-1 workload, encrypt then decrypt",
                "seconds": dt, "gpu_matches_oracle_on_sample": bool((gpu_ct == oct_).all() and (opt == sample).all())}
+        cpu["openssl_context"] = openssl_ecb(w.key, w.data, cores, 3.0, gpu_ct[: 1 << 20])
         # the sensor column (10^7 records) on the same cores: a bounded sample of its records
         col = workloads.sensor_records(2, 10_000_000)
         for name, kb in (("aes128", col.key128), ("aes256", col.key256)):
