@@ -759,9 +759,10 @@ HEADER = """// aes_bitslice_sbox.cuh -- GENERATED by gen_bitslice_sbox.py; do no
 //   S-box:          {fc} LOP3 ({fg} two-input gates before mapping), N = {fn}, L = 0x{fl:X}, GF(16) inverse as {fm} (tower {ft[1]}, seed {ft[3]})
 //   inverse S-box:  {ic} LOP3 ({ig} two-input gates before mapping), N = {inn}, L = 0x{il:X}, GF(16) inverse as {im} (tower {it[1]}, seed {it[3]})
 // No memory access, no branch: the circuit's time does not depend on data or key.
-// Each statement is one three-input table (its LOP3 immediate in the comment), written as a C
-// expression; on the device an empty asm fence after each keeps the compiler from merging
-// tables, so that each folds into that single instruction.
+// Each statement is one three-input table AES_SBOX_T(immediate, a, b, c, expression): on the
+// device one lop3 instruction with the table as its immediate, on the host (the CPU test of
+// the rounds) the same table as a C expression.  Left as C expressions on the device, the
+// compiler regrouped the tables inside the rolled round loop (84-87 instructions per S-box).
 #pragma once
 #include <cstdint>
 
@@ -771,9 +772,15 @@ HEADER = """// aes_bitslice_sbox.cuh -- GENERATED by gen_bitslice_sbox.py; do no
 #define AES_SBOX_FN inline
 #endif
 #if defined(__CUDA_ARCH__)
-#define AES_SBOX_FENCE(v) asm("" : "+r"(v))
+template <uint32_t L>
+__device__ __forceinline__ uint32_t aes_lop3(uint32_t a, uint32_t b, uint32_t c) {{
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(L));
+  return d;
+}}
+#define AES_SBOX_T(L, a, b, c, e) aes_lop3<L>(a, b, c)
 #else
-#define AES_SBOX_FENCE(v) ((void)0)
+#define AES_SBOX_T(L, a, b, c, e) (e)
 #endif
 
 namespace aesgb {{
@@ -807,10 +814,11 @@ def allocate(prog, outs: list[int]) -> tuple[dict, int]:
 
 
 def render(name: str, prog, outs: list[int]) -> str:
-    """The network as one function: each table is a C expression over its three operands, and
-    on the device its result passes an empty inline-asm fence, so the compiler cannot merge
-    tables (a subexpression shared by two tables would need an instruction of its own) and
-    ptxas folds each into one LOP3 while it schedules them freely; the fence emits nothing."""
+    """The network as one function: each table is AES_SBOX_T(immediate, a, b, c, expression),
+    one lop3 on the device (a statement of its own, so that ptxas schedules the tables freely
+    but cannot regroup them) and the C expression of the same table on the host.  Tables of
+    fewer than three leaves repeat the first leaf in the unused positions (the immediate does
+    not depend on them)."""
     args = ", ".join(f"uint32_t& x{i}" for i in range(8))
     nm = {i: f"i{i}" for i in range(8)}
     lines = [f"  const uint32_t i{i} = x{i};" for i in range(8)]
@@ -818,8 +826,8 @@ def render(name: str, prog, outs: list[int]) -> str:
         nm[v] = f"t{v}"
         ops = [nm[l] for l in leaves]
         ops += [ops[0]] * (3 - len(ops))
-        lines.append(f"  uint32_t t{v} = {c_expr(lop3_imm(t, len(leaves)), ops)};  // lop3 0x{t:02X}")
-        lines.append(f"  AES_SBOX_FENCE(t{v});")
+        imm = lop3_imm(t, len(leaves))
+        lines.append(f"  const uint32_t t{v} = AES_SBOX_T(0x{imm:02X}, {ops[0]}, {ops[1]}, {ops[2]}, {c_expr(imm, ops)});")
     for i, o in enumerate(outs):
         lines.append(f"  x{i} = {nm[o]};")
     return f"AES_SBOX_FN void {name}({args}) {{\n" + "\n".join(lines) + "\n}\n\n"
