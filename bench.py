@@ -679,8 +679,11 @@ def measure_served(aes, torch, dev, nreq: int, plain_gbs: float, closed_n: int =
     pool = aes.KeyPool(len(w0.pool_keys))
     pool.load_keys(0, np.stack(w0.pool_keys[:512]), 128)
     pool.load_keys(512, np.stack(w0.pool_keys[512:]), 256)
+    # the worker keeps polling for 2 ms after its last request or batch (one host core), so that
+    # requests arriving at least every 2 ms find it awake instead of paying a thread wake-up
     srv = aes.Server(pool, hbm_budget=1 << 30, max_inflight=1 << 21, nstreams=4, max_batch=8192,
-                     queue_capacity=1 << 21)
+                     queue_capacity=1 << 21, linger_us=2000)
+    out["server_cfg"] = {"nstreams": 4, "max_batch": 8192, "hbm_budget": 1 << 30, "linger_us": 2000}
     try:
         for rate in (1000.0, 3000.0, 10000.0, 30000.0, 100000.0, None):
             count = closed_n if rate is None else 10 * nreq if rate >= 1e5 else nreq

@@ -351,7 +351,10 @@ typedef struct {
                                submit returns AES_EAGAIN (>= 1; rounded up to a power of two) */
   uint32_t fail_every;      /* fault injection for tests: every n-th launch fails on the host
                                without touching the GPU (its requests end FAILED); 0 = off */
-  uint32_t reserved;
+  uint32_t linger_us;       /* microseconds the server's worker thread keeps polling (one host
+                               core busy) after its last admission or completion before it
+                               sleeps; requests that arrive within it skip a thread wake-up.
+                               0 = sleep as soon as nothing is queued or running */
 } aes_server_cfg;
 
 typedef struct {

@@ -66,7 +66,7 @@ def msg_dtype():
 class aes_server_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32), ("nstreams", ctypes.c_uint32),
                 ("max_batch", ctypes.c_uint32), ("queue_capacity", ctypes.c_uint32), ("fail_every", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("linger_us", ctypes.c_uint32)]
 
 
 class aes_request(ctypes.Structure):
@@ -513,8 +513,8 @@ class Server:
     """Continuous-batching request server (aes_server_*)."""
 
     def __init__(self, pool: KeyPool, hbm_budget: int = 1 << 30, max_inflight: int = 1 << 16, nstreams: int = 4,
-                 max_batch: int = 4096, queue_capacity: int = 1 << 16, fail_every: int = 0):
-        cfg = aes_server_cfg(hbm_budget, max_inflight, nstreams, max_batch, queue_capacity, fail_every, 0)
+                 max_batch: int = 4096, queue_capacity: int = 1 << 16, fail_every: int = 0, linger_us: int = 0):
+        cfg = aes_server_cfg(hbm_budget, max_inflight, nstreams, max_batch, queue_capacity, fail_every, linger_us)
         h = _VP()
         _check(lib().aes_server_create(ctypes.byref(cfg), pool.handle, ctypes.byref(h)))
         self.handle, self.pool = h, pool

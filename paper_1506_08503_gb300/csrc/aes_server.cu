@@ -362,12 +362,15 @@ constexpr uint64_t kRampBatch = 512;
 // The worker admits queued requests into batches and retires finished batches.  While a
 // batch is in flight it does not sleep: it polls the batches' done events between admissions
 // (yielding the core between rounds), so a batch is retired as soon as the GPU has finished
-// it; with nothing in flight it sleeps on cv_work.
+// it; with nothing in flight it keeps polling for cfg.linger_us after its last admission or
+// batch (a request that comes within that window finds it awake), then sleeps on cv_work.
 void worker_main(aes_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
+  const double linger = 1e-6 * s->cfg.linger_us;
+  double last_active = 0.0;  // last admission or batch on the GPU
   auto idle = [&](bool in_flight) {
-    if (in_flight || any_awaiting(s)) {
+    if (in_flight || any_awaiting(s) || (linger > 0.0 && now_s() - last_active < linger)) {
       lk.unlock();
       std::this_thread::yield();
       lk.lock();
@@ -378,6 +381,7 @@ void worker_main(aes_server* s) {
   for (;;) {
     lk.unlock();
     const bool in_flight = poll_completions(s);
+    if (in_flight && linger > 0.0) last_active = now_s();
     lk.lock();
     bool any_busy = false;
     int free_slot = -1;
@@ -426,6 +430,7 @@ void worker_main(aes_server* s) {
       continue;
     }
     s->admit = t;
+    if (linger > 0.0) last_active = now_s();
     StreamSlot& sl = s->slots[free_slot];
     sl.busy = true;
     sl.first = first;

@@ -310,3 +310,30 @@ def test_small_batches_take_the_one_launch_path(aes_lib_ready, orc):
                 got = hdst[o:o + L] if on_host[i] else got_dev[o:o + L]
                 want = oracle_crypt(orc, keys[int(reqs[i]["key_idx"])], data[o:o + L], int(reqs[i]["dir"]))
                 assert (got == want).all(), (count, i)
+
+
+def test_linger_keeps_worker_polling_and_results_exact(aes_lib_ready, orc):
+    """A server whose worker keeps polling for 3 ms after its last request (linger_us): requests
+    spaced 0.5 ms apart (inside the window) and 8 ms apart (after it, so the worker has gone to
+    sleep and must be woken) all complete with the oracle's output, and the server shuts down
+    cleanly while lingering."""
+    import time
+
+    import torch
+
+    rng = np.random.default_rng(49)
+    pool, keys = make_pool(rng)
+    with pool, aes.Server(pool, hbm_budget=16 << 20, nstreams=2, max_batch=16, linger_us=3000) as srv:
+        for gap in [0.0005] * 6 + [0.008] * 3 + [0.0005] * 3:
+            n = int(rng.integers(1, 300))
+            data = rng.integers(0, 256, 16 * n, dtype=np.uint8)
+            k, d = int(rng.integers(0, len(keys))), int(rng.integers(0, 2))
+            src = torch.from_numpy(data).cuda()
+            dst = torch.empty_like(src)
+            torch.cuda.synchronize()
+            t = srv.submit(k, d, src.data_ptr(), dst.data_ptr(), 16 * n, True, True)
+            assert srv.poll(t, 10_000_000) == aes.AES_REQ_DONE
+            assert (dst.cpu().numpy() == oracle_crypt(orc, keys[k], data, d)).all()
+            time.sleep(gap)
+        st = srv.stats()
+        assert st["completed"] == 12 and st["failed"] == 0
