@@ -59,29 +59,47 @@ ctr_kernel(const uint4* in, uint4* out, size_t nblocks, uint64_t ctr_hi, uint64_
   }
 }
 
+// HBM-bound: each thread issues kScanU independent 16-byte loads before it compares any, so
+// that more bytes are in flight per SM; loads at u * stride keep every warp instruction on 512
+// contiguous bytes.  Measured on one GB300, 10^7 records, 20 calls back to back: one load per
+// step 30.5-30.7 us per call, two 27.6-28.1, four 28.9-29.0 (eight per warp, contiguous, as two).
+constexpr int kScanU = 2;
+
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+
 __global__ void __launch_bounds__(256)
 scan_equal_kernel(const uint4* col, size_t n, uint4 needle, unsigned long long* matches, size_t max_matches,
                   unsigned long long* count) {
   const size_t stride = size_t(gridDim.x) * blockDim.x;
   const uint32_t lane = threadIdx.x & 31u;
-  // every lane of the warp runs the same number of iterations, so the ballot is warp-wide
+  // every lane of the warp runs the same number of iterations (the bound is tested on the
+  // warp's first index), so each ballot is warp-wide
   const size_t n_round = (n + 31) & ~size_t(31);
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i - lane < n_round; i += stride) {
-    bool hit = false;
-    if (i < n) {
-      uint4 v;
-      asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                   : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(col + i));
-      hit = v.x == needle.x && v.y == needle.y && v.z == needle.z && v.w == needle.w;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i - lane < n_round; i += kScanU * stride) {
+    uint4 v[kScanU];
+#pragma unroll
+    for (int u = 0; u < kScanU; ++u) {
+      const size_t j = i + u * stride;
+      v[u] = j < n ? ld_stream(col + j) : make_uint4(~needle.x, 0u, 0u, 0u);
     }
-    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, hit);
-    if (mask) {
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(mask));
-      base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (hit) {
-        const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
-        if (slot < max_matches) matches[slot] = i;
+#pragma unroll
+    for (int u = 0; u < kScanU; ++u) {
+      const size_t j = i + u * stride;
+      const bool hit = j < n && v[u].x == needle.x && v[u].y == needle.y && v[u].z == needle.z && v[u].w == needle.w;
+      const uint32_t mask = __ballot_sync(0xFFFFFFFFu, hit);
+      if (mask) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(mask));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (hit) {
+          const unsigned long long slot = base + __popc(mask & ((1u << lane) - 1u));
+          if (slot < max_matches) matches[slot] = j;
+        }
       }
     }
   }

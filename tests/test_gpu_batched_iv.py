@@ -242,3 +242,28 @@ def test_cbc_batched_many_messages(aes_lib_ready, orc, n):
         for i in np.nonzero((dirs == 0) & (lengths > 0))[0]:
             o, L = int(offsets[i]), int(lengths[i])
             assert np.array_equal(zz[o:o + L], data[o:o + L]), i
+
+
+def test_cbc_batched_encrypt_in_place(aes_lib_ready, orc):
+    """aes_cbc_batched encryption with the output buffer the input buffer (allowed for
+    encryption: each chain reads its next block before it overwrites the current one), 300
+    messages of 1-40 blocks with own keys and IVs, every message against the oracle."""
+    rng = np.random.default_rng(95)
+    n = 300
+    keys = [rng.integers(0, 256, b // 8, dtype=np.uint8) for b in (128, 192, 256)]
+    key_idx = rng.integers(0, len(keys), n).astype(np.uint32)
+    lengths = (rng.integers(1, 41, n) * 16).astype(np.int64)
+    offsets = np.concatenate([[0], np.cumsum(lengths)[:-1]]).astype(np.int64)
+    data = rng.integers(0, 256, int(lengths.sum()), dtype=np.uint8)
+    ivs = rng.integers(0, 256, (n, 16), dtype=np.uint8)
+    msgs = np.zeros(n, dtype=aes.msg_dtype())
+    msgs["key_idx"], msgs["offset"], msgs["length"] = key_idx, offsets, lengths
+    with aes.KeyPool(len(keys)) as pool:
+        for i, k in enumerate(keys):
+            pool.load_keys(i, k[None, :], 8 * len(k))
+        x = dev(data)
+        aes.aes_cbc_batched(pool, msgs, ivs, x.data_ptr(), x.data_ptr(), data.size)
+        got = host(x)
+        for i in range(n):
+            o, L = int(offsets[i]), int(lengths[i])
+            assert np.array_equal(got[o:o + L], orc.cbc_encrypt(keys[int(key_idx[i])], ivs[i], data[o:o + L])), i

@@ -67,3 +67,22 @@ def test_equality_scan_on_encrypted_sensor_column(aes_lib_ready, orc):
     needle = orc.encrypt_blocks(col.key128, rec[7]).tobytes()
     idx, k = aes.find_equal(enc, needle, max_matches=2)
     assert k >= 2 and idx.numel() == 2
+
+
+@pytest.mark.parametrize("n", [1, 5, 33, 311_297, 1_000_003])
+def test_equality_scan_ragged_sizes(aes_lib_ready, n):
+    """Record counts that end inside a warp, inside the first loads of a thread and past one
+    grid-wide step of four loads per thread; matches planted at the first and last records and
+    in between, checked against numpy record equality."""
+    import torch
+
+    rng = np.random.default_rng(6 + n)
+    rec = rng.integers(0, 256, (n, 16), dtype=np.uint8)
+    needle = rng.integers(0, 256, 16, dtype=np.uint8)
+    for dst in {0, n - 1, n // 2, n // 3}:
+        rec[dst] = needle
+    col = torch.from_numpy(rec.reshape(-1)).cuda()
+    idx, k = aes.find_equal(col, needle.tobytes())
+    want = np.flatnonzero((rec == needle).all(axis=1))
+    assert k == len(want)
+    assert (idx.cpu().numpy() == want).all()
