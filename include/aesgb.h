@@ -123,8 +123,9 @@ aes_status aes_set_auto_choice(int dir, int nr, int impl, int threads, int unrol
  * message per row, rows back to back; row i is chained: C_j = E(P_j xor C_{j-1}) with
  * C_{-1} = IV_i, and P_j = D(C_j) xor C_{j-1}.  d_ivs (device, 16-byte aligned) holds one
  * 16-byte IV for every row (iv_per_msg = 0, the appendix's repeated IV) or one per row
- * (iv_per_msg = 1, the IV matrix V of Section II).  Encryption runs one lane per message (the
- * chain is serial inside a message), decryption one lane per block.  Encryption may run in
+ * (iv_per_msg = 1, the IV matrix V of Section II).  Encryption is serial inside a message:
+ * up to 64 messages per SM run four lanes to a message (one per state column), more run one
+ * lane per message; decryption runs one lane per block.  Encryption may run in
  * place; decryption may not (each block needs the previous ciphertext): AES_EINVAL.  An empty
  * matrix returns AES_OK. */
 aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_ivs, int iv_per_msg, const void* d_in,
@@ -301,8 +302,9 @@ aes_status aes_crypt_batched_iv(aes_keypool* pool, const aes_msg* msgs, const ui
  * bytes; NULL means zero IVs), chained over its blocks: C_j = Cipher_K(P_j xor C_{j-1}) with
  * C_{-1} = IV for msgs[i].dir = AES_ENCRYPT, P_j = InvCipher_K(C_j) xor C_{j-1} for AES_DECRYPT.
  * msgs and the buffers follow aes_batch_run's rules (offsets index both buffers, whole blocks,
- * AES-128/192/256 keys mixed).  Encryption runs one lane per message (a chain is serial, so a
- * long message is as slow as its chain); decryption runs one lane per block.  A call with any
+ * AES-128/192/256 keys mixed).  Encryption is serial inside a message, so a long message is as
+ * slow as its chain: up to 64 encrypted messages per SM run four lanes to a message, more run
+ * one lane per message; decryption runs one lane per block.  A call with any
  * decryption message cannot run in place (AES_EINVAL).  Asynchronous on cuda_stream; the first
  * call on a pool allocates its descriptor buffers (kept with the pool, grown as needed).
  * Calls on one pool are serialised. */
