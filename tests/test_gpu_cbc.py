@@ -190,3 +190,23 @@ def test_encrypt_chain_shapes(aes_lib_ready, orc, per_sm, extra):
     back = aes.cbc(dev(ct), ks, dev(ivs), "decrypt")
     torch.cuda.synchronize()
     assert torch.equal(back, x)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (128, 16), (128, 256), (257, 128), (129, 255)],
+                         ids=lambda s: f"{s[0]}x{s[1]}")
+@pytest.mark.parametrize("key_bits", [128, 256])
+def test_decrypt_small_matrices(aes_lib_ready, orc, shape, key_bits):
+    """Decryption of arbitrary data (not only round trips) of small matrices, down to a single
+    block, and of a few thousand blocks up to 32896, with one IV per message and with one
+    shared IV, against the oracle's CBC."""
+    n, m = shape
+    rng = np.random.default_rng(90 + n * 7 + m + key_bits)
+    key = rng.integers(0, 256, key_bits // 8, dtype=np.uint8)
+    ks = aes.aes_key_expand(key.tobytes(), key_bits)
+    ct = rng.integers(0, 256, (n, 16 * m), dtype=np.uint8)
+    ivs = rng.integers(0, 256, (n, 16), dtype=np.uint8)
+    for iv_arg, iv_of in ((ivs, lambda i: ivs[i]), (ivs[0], lambda i: ivs[0])):
+        pt = aes.cbc(dev(ct), ks, dev(iv_arg), "decrypt").cpu().numpy()
+        rows = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 40)]))
+        for i in rows:
+            assert (pt[i] == orc.cbc_decrypt(key, iv_of(i), ct[i])).all(), (i, iv_arg.ndim)
