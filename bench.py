@@ -53,6 +53,10 @@ SEED = 1
 ALU_LANES, LDS_LANES = 64.0, 32.0
 TT_LDS, TT_ALU, BS_ALU = 160.0, 240.0, 22800.0 / 64.0
 SM_COUNT_NOMINAL, SM_MAX_MHZ_NOMINAL = 152, 2070.0
+# The bitsliced kernel's own instruction count on the integer ALU pipe per AES-128 block (LOP3 +
+# PRMT + SHF, from ncu's per-opcode counts at 2^24 blocks, profiles/bs_kernel_aes128_256MiB.md):
+# the ceiling of this circuit and layout, beside the gate-level bound of the best circuits.
+BS_KERNEL_ALU = {"encrypt": 511.5 + 16.0 + 12.0, "decrypt": 567.8 + 16.0 + 12.0}
 
 
 def blocks_per_sm_clock() -> float:
@@ -362,6 +366,13 @@ def measure_bitsliced(aes, torch, dev, x, n: int, key: bytes, sms: int, gpu: int
                 "decrypt_frac": out["decrypt_gbs"] / bound,
                 "bound_source": f"{sms} SMs x {SM_MAX_MHZ_NOMINAL:.0f} MHz x {ALU_LANES:.0f} lanes / "
                                 f"{BS_ALU} lane-ops per block x 16 B"})
+    for d in ("encrypt", "decrypt"):
+        kb = logic_bound_gbs(sms, SM_MAX_MHZ_NOMINAL, BS_KERNEL_ALU[d])
+        out[f"{d}_kernel_alu_bound_gbs"] = kb
+        out[f"{d}_frac_of_kernel_alu_bound"] = out[f"{d}_gbs"] / kb
+    out["kernel_alu_bound_source"] = (f"{sms} SMs x {SM_MAX_MHZ_NOMINAL:.0f} MHz x {ALU_LANES:.0f} lanes / the kernel's "
+                                      f"ALU-pipe instructions per block (ncu: {BS_KERNEL_ALU['encrypt']} encrypt, "
+                                      f"{BS_KERNEL_ALU['decrypt']} decrypt) x 16 B")
     del y, z
     return out
 
@@ -376,7 +387,8 @@ def summary_of(line: dict, sms: int) -> dict:
     bs = line.get("bitsliced")
     if bs:
         s["bitsliced_1GiB"] = {k: bs[k] for k in ("encrypt_gbs", "decrypt_gbs", "encrypt_frac", "decrypt_frac",
-                                                 "logic_bound_gbs")}
+                                                 "logic_bound_gbs", "encrypt_frac_of_kernel_alu_bound",
+                                                 "decrypt_frac_of_kernel_alu_bound")}
         s["bitsliced_1GiB"]["sm_mhz"] = bs["clocks"].get("sm_mhz")
     b = line.get("batched")
     if b:
