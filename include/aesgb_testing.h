@@ -32,6 +32,11 @@ int aes_testing_arena(size_t size, const int64_t* ops, size_t nops, int64_t* res
 int aes_testing_tune_cache_store(const char* path, const char* sig, int impl, int threads, int unroll, double us);
 int aes_testing_tune_cache_lookup(const char* path, const char* sig, int* impl, int* threads, int* unroll);
 
+/* The launch shape of CBC encryption with four lanes per chain for `chains` chains on a device
+ * of `sms` SMs: CTA threads, the warps of a CTA that run chains, grid, and chains per warp.
+ * Returns 0, or -1 for chains = 0 or sms < 1. */
+int aes_testing_cols_shape(uint64_t chains, int sms, unsigned* threads, unsigned* wpc, unsigned* grid, unsigned* cpw);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "aes_ttable.cuh"
+#include "aesgb_testing.h"
 
 namespace aesgb {
 namespace {
@@ -291,6 +292,17 @@ ColsShape cols_shape(uint64_t chains, int sms) {
 }  // namespace aesgb
 
 using namespace aesgb;
+
+extern "C" int aes_testing_cols_shape(uint64_t chains, int sms, unsigned* threads, unsigned* wpc, unsigned* grid,
+                                      unsigned* cpw) {
+  if (chains == 0 || sms < 1 || !threads || !wpc || !grid || !cpw) return -1;
+  const ColsShape sh = cols_shape(chains, sms);
+  *threads = sh.threads;
+  *wpc = sh.wpc;
+  *grid = sh.grid;
+  *cpw = sh.cpw;
+  return 0;
+}
 
 extern "C" aes_status aes_cbc_crypt(const aes_key_schedule* ks, const void* d_ivs, int iv_per_msg, const void* d_in,
                                     void* d_out, size_t nmsgs, size_t blocks_per_msg, int dir, void* cuda_stream) {

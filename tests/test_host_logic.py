@@ -26,6 +26,8 @@ def hooks(aes):
     lib.aes_testing_tune_cache_store.restype = ctypes.c_int
     lib.aes_testing_tune_cache_store.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_double]
+    lib.aes_testing_cols_shape.restype = ctypes.c_int
+    lib.aes_testing_cols_shape.argtypes = [ctypes.c_uint64, ctypes.c_int] + [ctypes.POINTER(ctypes.c_uint)] * 4
     lib.aes_testing_tune_cache_lookup.restype = ctypes.c_int
     lib.aes_testing_tune_cache_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, _IP, _IP, _IP]
     return lib
@@ -163,3 +165,27 @@ def test_tune_cache_store_and_lookup(hooks, tmp_path):
     # an entry that names no compiled candidate is ignored, so the tuner times instead
     assert hooks.aes_testing_tune_cache_lookup(path, b"dev|dec|nr12|log2n20", ctypes.byref(i), ctypes.byref(t),
                                                ctypes.byref(u)) == 0
+
+
+def cols_shape(hooks, chains, sms):
+    v = [ctypes.c_uint() for _ in range(4)]
+    rc = hooks.aes_testing_cols_shape(chains, sms, *[ctypes.byref(x) for x in v])
+    assert rc == 0
+    return tuple(x.value for x in v)  # threads, chain warps per CTA, grid, chains per warp
+
+
+@pytest.mark.parametrize("sms", [1, 7, 152])
+def test_cbc_cols_shape_covers_every_chain_in_one_pass(hooks, sms):
+    """The four-lanes-per-chain CBC launch for 1 .. 64 x sms chains: at most one CTA per SM, at
+    least 128 threads (the table fill), chain warps that fit the CTA, 1-8 chains per warp, one
+    chain per warp while there are at most 4 per SM, and enough chain slots for every chain at
+    once (the chains run side by side, none waits for another to finish)."""
+    for chains in list(range(1, 4 * sms + 2)) + [32 * sms, 32 * sms + 1, 64 * sms - 1, 64 * sms]:
+        threads, wpc, grid, cpw = cols_shape(hooks, chains, sms)
+        assert 1 <= grid <= sms and 1 <= wpc <= 8 and 1 <= cpw <= 8, chains
+        assert threads == max(128, 32 * wpc), chains
+        assert grid * wpc * cpw >= chains, chains
+        if chains <= 4 * sms:
+            assert cpw == 1, chains
+    assert hooks.aes_testing_cols_shape(0, sms, *[ctypes.byref(ctypes.c_uint()) for _ in range(4)]) == -1
+
