@@ -264,7 +264,9 @@ def openssl_ecb(key: np.ndarray, data: np.ndarray, cores: int, seconds: float, c
 
 def oracle_rate(orc, key, data_blocks: np.ndarray, cores: int, target_s: float, max_blocks: int) -> tuple[float, int]:
     """Calibrate: oracle blocks per second (encrypt) on `cores` threads."""
-    probe = min(max_blocks, max(cores * 256, 4096))
+    # large enough that thread start-up does not dominate (a 4096-block probe on 16 cores
+    # underestimated the rate about twofold, so samples came out at half their target time)
+    probe = min(max_blocks, max(cores * 4096, 16384))
     t = time.perf_counter()
     orc.encrypt_blocks(key, data_blocks[: probe * 16], threads=cores)
     dt = time.perf_counter() - t
